@@ -1,0 +1,330 @@
+"""Benchmark of the MH-DEOCT hot path on GB300: tree*sample evaluations per second.
+
+Workload (the large-scale DEOCT configuration): n = 10,000,000 samples, F = 10
+features U(0,1) quantised to 60,000 levels (uint16 ranks), K = 2 labels from a
+planted depth-4 tree with 2% flips; one step = rank-encode the feature matrix
+plus a full DEOCT fit of depth-4 trees with population 1024 and 50 generations
+(Algorithm 4): (50 + 1) * 1024 * 1e7 = 5.2e11 tree*sample evaluations.  The
+inputs (400 MB of features, 200 MB of ranks) are larger than the 129 MB L2,
+so no flush is needed between steps.
+
+  value  device-resident: X and y in HBM when the timed region starts.
+  e2e    the same metric through the public C ABI from pinned host buffers,
+         host->device copy of X, y and device->host copy of the fitted tree
+         inside the timed region.
+
+``--impl reference`` times the CPU oracle (the plain C implementation the
+tests check against) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "tree*sample evals/s"
+UNIT = "evals/s"
+WORKLOAD = dict(workload="large-deoct: n=1e7, F=10 U(0,1) quantised to 60000 levels (uint16 ranks), "
+                         "K=2 planted depth-4 tree 2% flips; step = rank encode + DEOCT depth 4, "
+                         "P=1024, G=50, M=0.5, CR=0.9",
+                n=10_000_000, F=10, K=2, depth=4, pop=1024, gens=50,
+                l2="inputs larger than L2 (X 400 MB, ranks 200 MB); no flush")
+INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_setup(gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _cpu_baseline(w, budget_s=12.0):
+    """The oracle as it stands on the host's cores: initial evaluation plus one DE
+    generation of the full population on a bounded prefix of the samples."""
+    import oracle
+    P, D = w["pop"], w["depth"]
+    n_try = 4000
+    X, y = w["X"], w["y"]
+    t0 = time.perf_counter()
+    ranks, nu = oracle.encode(X[:n_try])
+    oracle.de_run(ranks, nu, y[:n_try], w["K"], depth=D, P=P, G=1, seed=0)
+    dt = time.perf_counter() - t0
+    n_s = int(min(len(X), max(n_try, n_try * budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    ranks, nu = oracle.encode(X[:n_s])
+    oracle.de_run(ranks, nu, y[:n_s], w["K"], depth=D, P=P, G=1, seed=0)
+    dt = time.perf_counter() - t0
+    evals = 2 * P * n_s
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d samples of the workload: rank encode + initial evaluation + 1 DE "
+                      "generation of the P=1024 depth-4 population (%d evals, %.1f s)" % (n_s, evals, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, rank 0 only, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2311_06952_gb300 import datagen
+    w = dict(WORKLOAD)
+    n_s = 40_000
+    full = datagen.make_workload(3, n=n_s)
+    P, D = w["pop"], w["depth"]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ranks, nu = oracle.encode(full["X"])
+        oracle.de_run(ranks, nu, full["y"], full["K"], depth=D, P=P, G=1, seed=it)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    evals = 2 * P * n_s
+    ms = 1000.0 * float(np.mean(times))
+    value = evals / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(w, sample="each step: first %d samples, rank encode + initial evaluation "
+                                     "+ 1 DE generation (P=1024, depth 4)" % n_s),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d samples x 1024 trees x 2 evaluations per step" % n_s},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2311_06952_gb300 import build as _build
+    from paper_2311_06952_gb300 import datagen, deoct
+
+    rank, world, local = _dist_setup(args.gpus)
+    if rank == 0 or world > 1:
+        _build.build()
+    _barrier(world)
+    w = dict(WORKLOAD)
+    data = datagen.make_workload(3, n=args.n)
+    n, F, K = data["X"].shape[0], data["X"].shape[1], data["K"]
+    P, D, G = w["pop"], w["depth"], args.gens
+    stream = torch.cuda.current_stream()
+    ctx = deoct.Context(torch.cuda.current_device())
+    Xd = torch.from_numpy(data["X"]).cuda()
+    yd = torch.from_numpy(data["y"]).cuda()
+    prm = deoct.make_params(D, P, G, mut_f=0.5, cr=0.9, seed=0)
+    ranks = torch.empty((F, deoct.padded_ld(n, 2)), dtype=torch.int16, device="cuda")
+    nu = torch.empty(F, dtype=torch.int32, device="cuda")
+    evals_per_step = (G + 1) * P * n
+
+    def step(sid):
+        deoct.deoct_encode(ctx, Xd, 2, ranks_out=ranks, n_unique_out=nu)
+        ds = deoct.DeviceDataset(ranks, 2, nu, yd, n, F, K)
+        return deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)
+
+    for i in range(args.warmup):
+        step(rank)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    clk = ClockSampler(local) if rank == 0 else None
+    if clk:
+        clk.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        res = step(rank)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    clocks = clk.stop() if clk else None
+    st = ctx.stats()
+    ctx.set_timing(False)
+    ms_total = _max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = evals_per_step * world / (ms_step / 1000.0)
+
+    # ---- end to end through the public API, host buffers ----------------------
+    Xh = torch.from_numpy(data["X"]).pin_memory()
+    yh = torch.from_numpy(data["y"]).pin_memory()
+    h2d = Xh.numel() * 4 + yh.numel()
+    B = (1 << D) - 1
+    d2h = B * 2 + B * 4 + 8
+
+    def e2e_step(sid):
+        Xg = Xh.to("cuda", non_blocking=True)
+        yg = yh.to("cuda", non_blocking=True)
+        r_, nu_ = deoct.deoct_encode(ctx, Xg, 2)
+        ds = deoct.DeviceDataset(r_, 2, nu_, yg, n, F, K)
+        return deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)  # host outputs (sync)
+
+    e2e_step(rank)
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        e2e_step(rank)
+    torch.cuda.synchronize()
+    t_e2e = _max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = evals_per_step * world / (t_e2e / args.steps)
+
+    if rank != 0:
+        return 0
+    peaks, peak_kind = _peaks()
+    eval_ms = st["eval_ms"] / max(1, st["eval_timed"])
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    ops_per_eval = 2 * D + 1  # Algorithm 1: per level one comparison + one child step; one count
+    ops_per_launch = ops_per_eval * P * n
+    achieved = ops_per_launch / (eval_ms / 1000.0) / 1e12
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = nsm * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    bytes_per_launch = n * (F * 2 + 1)
+    hbm_achieved = bytes_per_launch / (eval_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": w, "gpu_launches": int(st["launches"]),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": args.traffic,
+                     "kernel": "eval_kernel<2,4,0> (population evaluator)",
+                     "ops_per_launch": ops_per_launch, "launch_ms": eval_ms,
+                     "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz (%s max clock)" % (
+                         nsm, INT32_LANES_PER_SM, sm_mhz, peak_kind),
+                     "hbm_view": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"],
+                                  "frac": hbm_achieved / peaks["hbm_gbs"],
+                                  "algorithmic_bytes_per_launch": bytes_per_launch,
+                                  "peak_kind": peak_kind}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "result": {"fitness": res[2], "train_accuracy": 1.0 - res[2] / n},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(dict(w, X=data["X"], y=data["y"]))
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    ap.add_argument("--gens", type=int, default=WORKLOAD["gens"])
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per evaluator launch, when a capture of this kernel exists")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

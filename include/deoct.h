@@ -1,0 +1,232 @@
+/*
+ * deoct.h -- C ABI of the GB300-native MH-DEOCT hot path.
+ *
+ * Method: Ren et al., "A GPU-Accelerated Moving-Horizon Algorithm for Training
+ * Deep Classification Trees on Large Datasets" (arXiv 2311.06952).  Section
+ * numbers, equations and algorithms below are the paper's.
+ *
+ * Conventions for every call:
+ *  - Return value: DEOCT_OK (0) or a negative deoct_status; the message of the
+ *    last failure on the calling thread is deoct_last_error_string().  No C++
+ *    exception crosses this boundary.
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    argument says "host".  The library never frees or keeps caller memory
+ *    beyond the call (except through the queued stream work of an async call).
+ *  - The library allocates only its own scratch, owned by the deoct_ctx and
+ *    released by deoct_destroy.  A context must not be used by two host threads
+ *    at once.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls marked "async" only enqueue work on it; calls marked
+ *    "sync" return after that work has finished and report device-side errors
+ *    (a bounded device wait that expired is DEOCT_ERR_TIMEOUT).
+ *  - Sizes: n <= 2^24 samples per dataset (thresholds are packed in 24 bits),
+ *    1 <= F <= 256 features, 1 <= K <= 255 classes, 1 <= depth <= 10,
+ *    4 <= P <= 4096 individuals.  Violations return DEOCT_ERR_INVALID.
+ */
+#ifndef DEOCT_H_
+#define DEOCT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DEOCT_API __attribute__((visibility("default")))
+#else
+#define DEOCT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DEOCT_OK = 0,
+  DEOCT_ERR_INVALID = -1, /* bad argument, NaN feature, rank width too small, ... */
+  DEOCT_ERR_OOM = -2,     /* device allocation of scratch failed */
+  DEOCT_ERR_CUDA = -3,    /* a CUDA runtime call failed */
+  DEOCT_ERR_TIMEOUT = -4, /* a bounded device-side wait ran out */
+  DEOCT_ERR_BUDGET = -5   /* request exceeds the configured memory budget */
+} deoct_status;
+
+/* deoct_params.flags */
+#define DEOCT_DITHER_M 0x1u /* M = rand(0,1) per (generation, individual), Section 3.3 */
+#define DEOCT_BATCHED 0x2u  /* moving horizon: one batched launch per level */
+
+typedef struct deoct_ctx deoct_ctx;
+
+/* A rank-encoded training set (Section 3.1 threshold sets, stored as ranks).
+ *  ranks     [F][ld] feature-major, uint16 (rank_bytes = 2) or uint32 (4):
+ *            ranks[p*ld + i] = number of distinct values of feature p below x_{i,p}.
+ *            16-byte aligned base and ld*rank_bytes % 16 == 0 enable TMA
+ *            staging; other layouts take a plain-load path.
+ *  n_unique  [F] uint32, n_p of Section 3.1 (>= 1).
+ *  labels    [n] uint8 class indices < K.
+ * All three are device pointers owned by the caller. */
+typedef struct {
+  const void* ranks;
+  int32_t rank_bytes;
+  int64_t ld;
+  const uint32_t* n_unique;
+  const uint8_t* labels;
+  int64_t n;
+  int32_t F;
+  int32_t K;
+} deoct_dataset;
+
+/* DE / moving-horizon knobs (Algorithm 2 and Algorithm 4 inputs).
+ *  depth    tree depth D (DEOCT) or final depth (moving horizon)
+ *  horizon  moving-horizon depth D_MH (Section 4); ignored by DEOCT calls
+ *  pop, gens population size N and generations G (Algorithm 4)
+ *  mut_f, cr mutation factor M and crossover probability CR (Eqs. mutation, crossover)
+ *  alpha, n_min  complexity weight and minimum leaf size (Eq. opt_all, Section 3.2)
+ *  flags    DEOCT_DITHER_M, DEOCT_BATCHED
+ *  seed     Philox4x64-10 key word 0 (key word 1 is the stream id of a call) */
+typedef struct {
+  int32_t depth;
+  int32_t horizon;
+  int32_t pop;
+  int32_t gens;
+  float mut_f;
+  float cr;
+  double alpha;
+  int32_t n_min;
+  uint32_t flags;
+  uint64_t seed;
+} deoct_params;
+
+/* Counters of kernel launches and (when timing is on) evaluator time. */
+typedef struct {
+  uint64_t launches;      /* every kernel this library launched */
+  uint64_t eval_launches; /* population-evaluator launches */
+  double eval_ms;         /* summed CUDA-event time of evaluator launches (timing on) */
+  uint64_t eval_timed;    /* evaluator launches included in eval_ms */
+} deoct_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context bound to CUDA device `device` (sync). *ctx receives it. */
+DEOCT_API int deoct_create(deoct_ctx** ctx, int device);
+/* Free the context's scratch (sync on the device).  NULL is accepted. */
+DEOCT_API int deoct_destroy(deoct_ctx* ctx);
+/* Message of the last failure on this thread ("" if none); static storage. */
+DEOCT_API const char* deoct_last_error_string(void);
+/* Library version string; static storage. */
+DEOCT_API const char* deoct_version(void);
+/* Enable (1) / disable (0) CUDA-event timing of every evaluator launch. */
+DEOCT_API int deoct_set_timing(deoct_ctx* ctx, int enable);
+/* Read the counters (sync on pending timing events) / reset them. */
+DEOCT_API int deoct_get_stats(deoct_ctx* ctx, deoct_stats* out);
+DEOCT_API int deoct_reset_stats(deoct_ctx* ctx);
+
+/* ---- a1: rank encoder ----------------------------------------------------
+ * Section 3.1: the threshold set B_p of feature p is built from its sorted
+ * unique values; a sample's position among them (its dense rank) decides every
+ * threshold test, so the encoder emits ranks and n_p ("only need to generate
+ * once").  Ranks are taken on the raw float32 values (monotone min-max scaling
+ * leaves them unchanged); -0.0 equals +0.0.
+ *  X          [n][F] float32 row-major (device, caller-owned)
+ *  rank_bytes 2 (uint16 ranks, needs every n_p <= 65536) or 4
+ *  ranks_out  [F][ld] (device); only columns 0..n-1 are written
+ *  n_unique_out [F] uint32 (device)
+ * sync.  DEOCT_ERR_INVALID on NaN, on n_p > 65536 with rank_bytes = 2 (the
+ * outputs are then unspecified), or on bad sizes. */
+DEOCT_API int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
+                 void* ranks_out, int64_t ld, uint32_t* n_unique_out, void* stream);
+
+/* ---- a2: decoding (Eq. aenc, Eq. benc) ------------------------------------
+ * genes [P][2B] float32, individual s_r = [ahat_1..ahat_B, bhat_1..bhat_B],
+ * B = 2^depth - 1.  a_t = floor(ahat_t) clamped to {0..F} (0 = no split);
+ * theta_t = min(floor(bhat_t * (n_p + 1)), n_p - 1) for p = a_t - 1 (the rank
+ * form of b_t = beta_{a_t, i}, i = floor(bhat_t (n_p+1)) + 1, where the last
+ * threshold 1 of B_p routes like the one before it), theta_t = 0 when a_t = 0.
+ *  a_out [P][B] uint16, theta_out [P][B] uint32 (device).  async. */
+DEOCT_API int deoct_decode_population(deoct_ctx* ctx, const deoct_dataset* ds, const float* genes,
+                            int32_t P, int32_t depth, uint16_t* a_out, uint32_t* theta_out,
+                            void* stream);
+
+/* ---- a3 + a4: population fitness evaluation (Algorithm 1, Section 3.2) ----
+ * Every selected sample is routed through every tree (node t -> 2t if
+ * rank[a_t - 1][i] < theta_t else 2t + 1; a_t = 0 -> right) and
+ * counts[r][leaf][y_i] is incremented (the class count matrix Zhat).  Each
+ * tree's misclassification count n - sum_leaf max_k Zhat (the loss identity
+ * of Section 2) is returned in errors_out.
+ *  sample_idx [n_sub] int32 indices into the dataset's samples, or NULL for
+ *             all n samples (then n_sub must equal ds->n)
+ *  a, theta   [P][B] decoded trees (a in {0..F}); a > F is DEOCT_ERR_INVALID
+ *             reported by the next sync call, and the node then routes right
+ *  counts_out [P][2^depth][K] uint32, or NULL
+ *  errors_out [P] uint32, or NULL
+ * async. */
+DEOCT_API int deoct_eval_population(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                          int64_t n_sub, const uint16_t* a, const uint32_t* theta, int32_t P,
+                          int32_t depth, uint32_t* counts_out, uint32_t* errors_out,
+                          void* stream);
+
+/* ---- a5: DE (Algorithm 4) -------------------------------------------------
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11) with key
+ * (params->seed, stream_id) and counter (generation, individual, block, 0);
+ * draw s of an individual is the (s % 8)-th 32-bit half (low first) of block
+ * s / 8.  Per (g, r): draw 0 -> r1, 1 -> r2 (distinct from r and each other,
+ * multiply-shift maps), 2 -> q_rand, 3 -> M when dithered, 4 + q -> rand(0,1)
+ * of gene q; uniform = (draw >> 8) * 2^-24.  Gene arithmetic is float32 with
+ * one rounding per operation: v = s_best + M (s_r1 - s_r2) (Eq. mutation),
+ * clamped to [0, largest float below the gene bound]; u_q = v_q if
+ * rand <= CR or q = q_rand else s_q (Eq. crossover); u replaces s iff
+ * f(u) <= f(s) (Eq. selection); best = lowest index of the minimal fitness,
+ * taken from the previous generation (Section 3.3).  Fitness is
+ * f = errors + V + alpha * #splits in double (Section 3.2).
+ *
+ * deoct_de_init: S^1 of Algorithm 4 -- slots 0..S-1 take `seeds` [S][2B]
+ * (device, nullable when S = 0), the others are uniform in the gene range
+ * (generation tag 0, draw q for gene q); evaluates it.
+ *  pop [P][2B] float32 out, fitness [P] double out, best [1] int32 out. async.
+ * deoct_de_step: one generation g >= 1: trial population from (pop, best),
+ * evaluation, selection; pop / fitness / best are updated in place. async. */
+DEOCT_API int deoct_de_init(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                  int64_t n_sub, const deoct_params* params, uint64_t stream_id,
+                  const float* seeds, int32_t S, float* pop, double* fitness, int32_t* best,
+                  void* stream);
+DEOCT_API int deoct_de_step(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                  int64_t n_sub, const deoct_params* params, uint64_t stream_id,
+                  int32_t generation, float* pop, double* fitness, int32_t* best, void* stream);
+
+/* DEOCT on one (sub)problem: deoct_de_init, then generations 1..G.  Writes the
+ * best tree's decoded nodes to host arrays a_out [B] (uint16) and theta_out [B],
+ * its fitness to *fitness_out (host), and, when pop_out is not NULL, the final
+ * population [P][2B] to device memory.  sync. */
+DEOCT_API int deoct_fit_subtree(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                      int64_t n_sub, const deoct_params* params, uint64_t stream_id,
+                      const float* seeds, int32_t S, uint16_t* a_out, uint32_t* theta_out,
+                      double* fitness_out, float* pop_out, void* stream);
+
+/* ---- a6 / a7: moving-horizon DEOCT (Algorithm 2, Section 4) ---------------
+ * Nodes are visited level by level (root depth 0).  A node whose sample set
+ * X_t has more than n_min samples and at least two classes is solved with
+ * horizon D_t = min(D_MH, D - depth(t)): D_t >= 2 by DEOCT of depth D_t on X_t
+ * (Philox stream id = t, the node's 1-based BFS index; no warm starts), D_t = 1
+ * by exhaustive depth-1 search (fewest fitness, then no split, lowest feature,
+ * lowest threshold); the root node of the solution is kept.  Other nodes get
+ * a_t = 0, theta_t = 0.  Thresholds are the global ranks.
+ * DEOCT_BATCHED in params->flags solves all nodes of a level in one batched
+ * launch per generation over a compacted sample index; otherwise each node is
+ * a separate DEOCT (the plain per-node form).  Both give identical trees.
+ *  a_out [2^D - 1] uint16, theta_out [2^D - 1] uint32, leaf_class_out [2^D]
+ *  uint8 (Eq. opt_c on the whole set, lowest class on ties): host arrays.
+ *  kind_out [2^D - 1] int32 (0 artificial, 1 depth-1 search, 2 DEOCT) and
+ *  node_fit_out [2^D - 1] double: host, nullable.  sync. */
+DEOCT_API int deoct_fit_moving_horizon(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* params,
+                             uint16_t* a_out, uint32_t* theta_out, uint8_t* leaf_class_out,
+                             int32_t* kind_out, double* node_fit_out, void* stream);
+
+/* Exhaustive depth-1 subtree (the bottom level of Algorithm 2): the
+ * minimum-fitness tree among "no split" and every (feature p, theta in
+ * 0..n_p-1) on the selected samples, first in the order (no split, p, theta).
+ * Host outputs *a_out (0..F), *theta_out, *fitness_out.  sync. */
+DEOCT_API int deoct_depth1_search(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                        int64_t n_sub, int32_t n_min, double alpha, uint16_t* a_out,
+                        uint32_t* theta_out, double* fitness_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEOCT_H_ */

@@ -1,0 +1,284 @@
+// de.cu -- device-side DEOCT step (Algorithm 4; Eqs. mutation, crossover,
+// selection; the fitness of Section 3.2) and tree decoding (Eq. aenc, Eq. benc).
+//
+// One CTA per subproblem.  A step kernel does, in order and as its flags ask:
+//   DE_FIRST  fitness of the just-evaluated initial population, best;
+//   DE_SELECT fitness of the just-evaluated trials, Eq. selection, best;
+//   DE_TRIAL  trial vectors of generation g from (population, best), their
+//             decoded nodes for the evaluator, and zeroed class counts.
+// So one generation is two launches: evaluator, step(SELECT|TRIAL).  Gene
+// arithmetic is float32 with one rounding per operation (__fsub_rn, __fmul_rn,
+// __fadd_rn); random numbers come from Philox4x64-10 keyed by (seed, stream).
+#include "internal.cuh"
+
+namespace deoct {
+
+namespace {
+
+__device__ __forceinline__ const DEProb& prob_of(const DEArgs& a) {
+  return a.probs ? a.probs[blockIdx.x] : a.single;
+}
+
+// Fitness of Section 3.2 from the class counts of individual r:
+// f = (errors + V) + alpha * splits, errors = n - sum_leaf max_k count,
+// V = #{leaf : 0 < n_leaf < n_min}, splits = #{t : a_t >= 1} (ahat_t >= 1).
+__device__ double fitness_of(const uint32_t* __restrict__ c, const float* __restrict__ genes, int B,
+                             int L, int K, int64_t n_valid, int n_min, double alpha) {
+  int64_t correct = 0;
+  uint32_t v = 0;
+  for (int l = 0; l < L; ++l) {
+    uint32_t mx = 0;
+    int64_t nl = 0;
+    for (int k = 0; k < K; ++k) {
+      uint32_t x = c[l * K + k];
+      mx = x > mx ? x : mx;
+      nl += x;
+    }
+    correct += mx;
+    if (nl > 0 && nl < n_min) v += 1;
+  }
+  uint32_t splits = 0;
+  for (int t = 0; t < B; ++t) splits += genes[t] >= 1.0f ? 1u : 0u;
+  const int64_t errors = n_valid - correct;
+  return __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(alpha, (double)splits));
+}
+
+__device__ __forceinline__ float clamp_gene(float v, float hi) {
+  v = v < 0.0f ? 0.0f : v;
+  return v > hi ? hi : v;
+}
+
+// block-wide argmin (lowest index among minimal values); result in *best_s
+__device__ void block_argmin(const double* __restrict__ fit, int P, int* best_s, double* red_f,
+                             int* red_i) {
+  double bf = 0.0;
+  int bi = -1;
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    double f = fit[r];
+    if (bi < 0 || f < bf) {
+      bf = f;
+      bi = r;
+    }
+  }
+  // warp reduce
+  for (int off = 16; off > 0; off >>= 1) {
+    double of = __shfl_down_sync(0xFFFFFFFFu, bf, off);
+    int oi = __shfl_down_sync(0xFFFFFFFFu, bi, off);
+    if (oi >= 0 && (bi < 0 || of < bf || (of == bf && oi < bi))) {
+      bf = of;
+      bi = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red_f[warp] = bf;
+    red_i[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double f0 = red_f[0];
+    int i0 = red_i[0];
+    for (int w = 1; w < nw; ++w) {
+      int oi = red_i[w];
+      double of = red_f[w];
+      if (oi >= 0 && (i0 < 0 || of < f0 || (of == f0 && oi < i0))) {
+        f0 = of;
+        i0 = oi;
+      }
+    }
+    *best_s = i0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
+  const DEProb& pb = prob_of(a);
+  const int P = a.P, D = a.depth, B = (1 << D) - 1, m = 2 * B, L = 1 << D;
+  const float ub_a = (float)(pb.F + 1);
+  const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    float* g = pb.pop + (int64_t)r * m;
+    if (r < pb.S) {
+      for (int q = 0; q < m; ++q) g[q] = pb.seeds[(int64_t)r * m + q];
+    } else {
+      U64x4 blk;
+      for (int q = 0; q < m; ++q) {
+        if ((q & 7) == 0) blk = philox4x64_10(0ull, (uint64_t)r, (uint64_t)(q >> 3), 0ull, a.seed,
+                                              pb.stream_id);
+        const float u = u01(draw_from_block(blk, (uint32_t)q));
+        const bool is_a = q < B;
+        g[q] = clamp_gene(__fmul_rn(u, is_a ? ub_a : 1.0f), is_a ? hi_a : hi_b);
+      }
+    }
+    for (int t = 0; t < B; ++t) {
+      int av;
+      uint32_t th;
+      decode_gene_pair(g[t], g[B + t], pb.F, pb.n_unique, &av, &th);
+      pb.nodes[(int64_t)r * B + t] = pack_node(av, th);
+    }
+  }
+  uint32_t* cnt = pb.counts;
+  const int64_t total = (int64_t)P * L * pb.K;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) cnt[e] = 0;
+  if (threadIdx.x == 0 && pb.gen) *pb.gen = 1;
+}
+
+__global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags) {
+  __shared__ double red_f[32];
+  __shared__ int red_i[32];
+  __shared__ int best_s;
+  __shared__ int g_s;
+  const DEProb& pb = prob_of(a);
+  const int P = a.P, D = a.depth, B = (1 << D) - 1, m = 2 * B, L = 1 << D, K = pb.K;
+
+  if (threadIdx.x == 0) g_s = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
+
+  if (flags & (DE_FIRST | DE_SELECT)) {
+    const bool first = (flags & DE_FIRST) != 0;
+    for (int r = threadIdx.x; r < P; r += blockDim.x) {
+      const float* genes = (first ? pb.pop : pb.trial) + (int64_t)r * m;
+      const double f = fitness_of(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
+                                  a.n_min, a.alpha);
+      if (first) {
+        pb.fit[r] = f;
+      } else {
+        pb.fit_trial[r] = f;
+        if (f <= pb.fit[r]) {  // Eq. selection: ties go to the trial
+          float* dst = pb.pop + (int64_t)r * m;
+          for (int q = 0; q < m; ++q) dst[q] = genes[q];
+          pb.fit[r] = f;
+        }
+      }
+    }
+    __syncthreads();
+    block_argmin(pb.fit, P, &best_s, red_f, red_i);
+    if (threadIdx.x == 0) *pb.best = best_s;
+  } else {
+    if (threadIdx.x == 0) best_s = *pb.best;
+    __syncthreads();
+  }
+
+  if (!(flags & DE_TRIAL)) return;
+  const int g = g_s;
+  if (g < 1 || g > a.G) return;  // device-driven replay past the last generation
+  const int best = best_s;
+  const float ub_a = (float)(pb.F + 1);
+  const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
+  const float* sb = pb.pop + (int64_t)best * m;
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
+    U64x4 blk = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
+    const uint32_t x0 = draw_from_block(blk, 0), x1 = draw_from_block(blk, 1);
+    const uint32_t x2 = draw_from_block(blk, 2), x3 = draw_from_block(blk, 3);
+    int r1 = (int)below(x0, (uint32_t)(P - 1));
+    if (r1 >= r) r1 += 1;
+    int r2 = (int)below(x1, (uint32_t)(P - 2));
+    const int lo = r < r1 ? r : r1, hi = r < r1 ? r1 : r;
+    if (r2 >= lo) r2 += 1;
+    if (r2 >= hi) r2 += 1;
+    const int qrand = (int)below(x2, (uint32_t)m);
+    const float M = a.dither ? u01(x3) : a.M;
+    const float* s1 = pb.pop + (int64_t)r1 * m;
+    const float* s2 = pb.pop + (int64_t)r2 * m;
+    const float* sr = pb.pop + (int64_t)r * m;
+    float* u = pb.trial + (int64_t)r * m;
+    for (int q = 0; q < m; ++q) {
+      const uint32_t s = 4u + (uint32_t)q;
+      if ((s & 7u) == 0u)
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)(s >> 3), 0ull, a.seed,
+                            pb.stream_id);
+      const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
+      const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
+      const float rq = u01(draw_from_block(blk, s));
+      u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
+    }
+    for (int t = 0; t < B; ++t) {
+      int av;
+      uint32_t th;
+      decode_gene_pair(u[t], u[B + t], pb.F, pb.n_unique, &av, &th);
+      pb.nodes[(int64_t)r * B + t] = pack_node(av, th);
+    }
+  }
+  const int64_t total = (int64_t)P * L * K;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) pb.counts[e] = 0;
+  if (threadIdx.x == 0 && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
+}
+
+__global__ void decode_kernel(const float* __restrict__ genes, int P, int B, int F,
+                              const uint32_t* __restrict__ n_unique, uint16_t* __restrict__ a_out,
+                              uint32_t* __restrict__ th_out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)P * B) return;
+  int64_t r = e / B;
+  int t = (int)(e - r * B);
+  int av;
+  uint32_t th;
+  decode_gene_pair(genes[r * 2 * B + t], genes[r * 2 * B + B + t], F, n_unique, &av, &th);
+  a_out[e] = (uint16_t)av;
+  th_out[e] = th;
+}
+
+__global__ void best_extract_kernel(const float* __restrict__ pop, const double* __restrict__ fit,
+                                    const int32_t* __restrict__ best, int B, int F,
+                                    const uint32_t* __restrict__ n_unique, uint16_t* __restrict__ a_out,
+                                    uint32_t* __restrict__ th_out, double* __restrict__ fit_out) {
+  const int b = *best;
+  const float* g = pop + (int64_t)b * 2 * B;
+  for (int t = threadIdx.x; t < B; t += blockDim.x) {
+    int av;
+    uint32_t th;
+    decode_gene_pair(g[t], g[B + t], F, n_unique, &av, &th);
+    a_out[t] = (uint16_t)av;
+    th_out[t] = th;
+  }
+  if (threadIdx.x == 0) *fit_out = fit[b];
+}
+
+int block_for(int P) {
+  int b = ((P + 31) / 32) * 32;
+  if (b > 1024) b = 1024;
+  if (b < 128) b = 128;
+  return b;
+}
+
+}  // namespace
+
+int de_launch_init(deoct_ctx* ctx, const DEArgs& a, cudaStream_t s) {
+  const int nprob = a.probs ? a.nprob : 1;
+  if (nprob <= 0) return DEOCT_OK;
+  de_init_kernel<<<nprob, block_for(a.P), 0, s>>>(a);
+  count_launch(ctx);
+  return check_launch("de_init_kernel");
+}
+
+int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream_t s) {
+  const int nprob = a.probs ? a.nprob : 1;
+  if (nprob <= 0) return DEOCT_OK;
+  de_step_kernel<<<nprob, block_for(a.P), 0, s>>>(a, g, flags);
+  count_launch(ctx);
+  return check_launch("de_step_kernel");
+}
+
+int launch_best_extract(deoct_ctx* ctx, const float* pop, const double* fit, const int32_t* best,
+                        int depth, int F, const uint32_t* n_unique, uint16_t* a_out,
+                        uint32_t* theta_out, double* fit_out, cudaStream_t s) {
+  best_extract_kernel<<<1, 256, 0, s>>>(pop, fit, best, (1 << depth) - 1, F, n_unique, a_out,
+                                        theta_out, fit_out);
+  count_launch(ctx);
+  return check_launch("best_extract_kernel");
+}
+
+int launch_decode(deoct_ctx* ctx, const float* genes, int P, int depth, int F,
+                  const uint32_t* n_unique, uint16_t* a_out, uint32_t* theta_out,
+                  cudaStream_t s) {
+  const int B = (1 << depth) - 1;
+  const int64_t total = (int64_t)P * B;
+  if (total <= 0) return DEOCT_OK;
+  decode_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(genes, P, B, F, n_unique, a_out,
+                                                               theta_out);
+  count_launch(ctx);
+  return check_launch("decode_kernel");
+}
+
+}  // namespace deoct

@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integers (ranks, counts, errors) and the DE trajectory (float32 genes, double
+fitness, best index) must agree bit for bit: both sides take every
+float decision in the same precision with one rounding per operation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_06952_gb300 import datagen
+
+from gpu_helpers import ctx, gpu_dataset, ranks_np, to_dev, u16, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c():
+    from paper_2311_06952_gb300 import build
+    build.build()
+    return ctx()
+
+
+def _rng(s):
+    return np.random.Generator(np.random.PCG64(s))
+
+
+# --------------------------------------------------------------------------
+# a1: rank encoder
+# --------------------------------------------------------------------------
+
+def _encode_case(name):
+    rng = _rng(sum(name.encode()))
+    if name == "w0":
+        w = datagen.make_workload(0)
+        return w["X"], 2
+    if name == "w1_small":
+        return datagen.make_workload(1, n=20000)["X"], 4
+    if name == "w3_small":
+        return datagen.make_workload(3, n=150_001)["X"], 2
+    if name == "ties_signed_zero":
+        X = np.round(rng.normal(size=(4097, 5)), 1).astype(np.float32)
+        X[::7, 0] = -0.0
+        X[::5, 0] = 0.0
+        X[:, 3] = 2.0
+        X[5, 4] = np.inf
+        X[6, 4] = -np.inf
+        return X, 2
+    if name == "one_sample":
+        return np.array([[3.0, -1.0]], np.float32), 4
+    if name == "wide_F":
+        return rng.random((3000, 131)).astype(np.float32), 4
+    if name == "continuous_u32":
+        return rng.lognormal(size=(70_000, 3)).astype(np.float32), 4
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["w0", "w1_small", "w3_small", "ties_signed_zero", "one_sample",
+                                  "wide_F", "continuous_u32"])
+def test_encode_bit_exact(c, name):
+    X, rb = _encode_case(name)
+    y = np.zeros(len(X), np.uint8)
+    ds = gpu_dataset(c, X, y, 2, rb)
+    r_ref, nu_ref = oracle.encode(X)
+    np.testing.assert_array_equal(u32(ds.n_unique), nu_ref)
+    np.testing.assert_array_equal(ranks_np(ds), r_ref)
+
+
+def test_encode_rejects_nan_and_narrow_width(c):
+    from paper_2311_06952_gb300 import deoct
+    X = np.zeros((100, 2), np.float32)
+    X[50, 1] = np.nan
+    with pytest.raises(deoct.DeoctError) as e:
+        gpu_dataset(c, X, np.zeros(100, np.uint8), 2, 4)
+    assert e.value.code == deoct.DEOCT_ERR_INVALID
+    X = np.arange(70000, dtype=np.float32)[:, None]
+    with pytest.raises(deoct.DeoctError):
+        gpu_dataset(c, X, np.zeros(70000, np.uint8), 2, 2)
+    # the context stays usable after both errors
+    X = np.arange(10, dtype=np.float32)[:, None]
+    ds = gpu_dataset(c, X, np.zeros(10, np.uint8), 2, 2)
+    assert u32(ds.n_unique)[0] == 10
+
+
+# --------------------------------------------------------------------------
+# a3 + a4: evaluator
+# --------------------------------------------------------------------------
+
+EVAL_CASES = [
+    # (n, F, K, depth, P, rank_bytes, subset, seed)
+    (1000, 8, 2, 2, 64, 2, False, 0),
+    (5001, 6, 3, 3, 40, 4, False, 1),
+    (5001, 6, 3, 3, 40, 2, True, 2),
+    (33, 3, 2, 1, 7, 2, False, 3),
+    (1, 2, 2, 2, 5, 4, False, 4),
+    (20000, 10, 4, 4, 300, 2, False, 5),   # several tree groups, K*L = 64 (2 bins per lane)
+    (12345, 5, 10, 3, 50, 4, False, 6),    # K*L = 80: 3 bins per lane
+    (9000, 7, 2, 5, 33, 2, False, 7),      # depth 5 ballot path
+    (9000, 7, 3, 6, 20, 4, False, 8),      # depth 6: shared-atomic path
+    (4000, 4, 2, 8, 9, 2, True, 9),        # depth 8, gathered subset
+    (70000, 3, 5, 4, 17, 4, False, 10),
+]
+
+
+@pytest.mark.parametrize("case", EVAL_CASES, ids=[str(c_[:7]) for c_ in EVAL_CASES])
+def test_eval_bit_exact(c, case):
+    from paper_2311_06952_gb300 import deoct
+    n, F, K, depth, P, rb, subset, seed = case
+    rng = _rng(100 + seed)
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ds = gpu_dataset(c, X, y, K, rb)
+    ranks, nu = oracle.encode(X)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    idx = None
+    if subset:
+        idx = np.sort(rng.choice(n, max(1, n // 3), replace=False)).astype(np.int32)
+        idx = idx[rng.permutation(len(idx))]  # any order
+    counts, errors = deoct.deoct_eval_population(
+        c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth,
+        sample_idx=None if idx is None else to_dev(idx))
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth, idx=idx)
+    _, ref_err, _, _ = oracle.fitness(ref, a, n if idx is None else len(idx))
+    np.testing.assert_array_equal(u32(counts), ref)
+    np.testing.assert_array_equal(u32(errors), ref_err)
+
+
+def test_eval_workload1_full_size(c):
+    """Population-evaluation workload at its full size: n=1e5, F=20, K=3, 256 depth-3 trees."""
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(1)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], w["rank_bytes"])
+    ranks, nu = oracle.encode(w["X"])
+    np.testing.assert_array_equal(ranks_np(ds), ranks)
+    a, th = datagen.random_population(nu, w["P"], w["depth"], _rng(w["pop_seed"]))
+    counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), w["depth"])
+    ref = oracle.eval_counts(ranks, w["y"], w["K"], a, th, w["depth"])
+    np.testing.assert_array_equal(u32(counts), ref)
+
+
+@pytest.mark.slow
+def test_eval_workload3_full_size_sampled(c):
+    """Large-scale workload at full size (n=1e7, 1024 depth-4 trees): every tree on the
+    GPU, a sample of trees recomputed one by one by the oracle."""
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(3)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], w["rank_bytes"])
+    rng = _rng(33)
+    nu = u32(ds.n_unique)
+    a, th = datagen.random_population(nu, w["P"], w["depth"], rng, allow_nosplit=True)
+    counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), w["depth"])
+    counts = u32(counts)
+    # invariants on every tree
+    assert np.all(counts.sum(axis=(1, 2)) == w["X"].shape[0])
+    ranks = ranks_np(ds)
+    pick = [0, 1, 511, 1023]
+    ref = oracle.eval_counts(ranks, w["y"], w["K"], a[pick], th[pick], w["depth"])
+    np.testing.assert_array_equal(counts[pick], ref)
+    # and the ranks themselves against the oracle on a few features
+    r_ref, nu_ref = oracle.encode(w["X"][:, :2])
+    np.testing.assert_array_equal(ranks[:2], r_ref)
+
+
+# --------------------------------------------------------------------------
+# a2 + a5: decoding and the DE trajectory
+# --------------------------------------------------------------------------
+
+def test_decode_bit_exact(c):
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(5)
+    X = np.round(rng.random((3000, 7)), 2).astype(np.float32)
+    X[:, 6] = 1.0
+    ds = gpu_dataset(c, X, np.zeros(3000, np.uint8), 2, 2)
+    _, nu = oracle.encode(X)
+    genes = datagen.random_genes(500, 3, 7, rng)
+    genes[0] = np.nextafter(np.float32([8] * 7 + [1.0] * 7), np.float32(0))
+    genes[1] = 0.0
+    a, th = deoct.deoct_decode_population(c, ds, to_dev(genes), 3)
+    a_ref, th_ref = oracle.decode(genes, 3, nu)
+    np.testing.assert_array_equal(u16(a).astype(np.int32), a_ref)
+    np.testing.assert_array_equal(u32(th), th_ref)
+
+
+DE_CASES = [
+    # (workload/n, depth, P, G, CR, dither, subset, K override, seed, stream)
+    ("w0", 2, 64, 100, 0.9, False, False, 0, 0),
+    ("w0", 3, 32, 25, 0.1, True, False, 7, 5),
+    ("w0", 2, 16, 30, 0.5, False, True, 3, 9),
+    ("rand_k3", 3, 24, 20, 0.9, False, False, 11, 1),
+]
+
+
+@pytest.mark.parametrize("case", DE_CASES, ids=[str(x[:4]) for x in DE_CASES])
+def test_de_trajectory_bit_exact(c, case):
+    from paper_2311_06952_gb300 import deoct
+    name, depth, P, G, CR, dither, subset, seed, stream = case
+    if name == "w0":
+        w = datagen.make_workload(0)
+        X, y, K = w["X"], w["y"], w["K"]
+    else:
+        rng = _rng(77)
+        X = np.round(rng.random((2500, 6)), 2).astype(np.float32)
+        y = rng.integers(0, 3, 2500).astype(np.uint8)
+        K = 3
+    ds = gpu_dataset(c, X, y, K, 2)
+    ranks, nu = oracle.encode(X)
+    idx = None
+    if subset:
+        idx = np.sort(_rng(seed).choice(len(X), len(X) // 2, replace=False)).astype(np.int32)
+    ref = oracle.de_run(ranks, nu, y, K, depth=depth, P=P, G=G, CR=CR, seed=seed, stream=stream,
+                        dither=dither, idx=idx, history=True)
+    flags = deoct.DEOCT_DITHER_M if dither else 0
+    prm = deoct.make_params(depth, P, G, cr=CR, seed=seed, flags=flags)
+    sidx = None if idx is None else to_dev(idx)
+    pop, fit, best = deoct.deoct_de_init(c, ds, prm, stream_id=stream, sample_idx=sidx)
+    np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), ref["pop_hist"][0].view(np.uint32))
+    np.testing.assert_array_equal(fit.cpu().numpy(), ref["fit_hist"][0])
+    for g in range(1, G + 1):
+        deoct.deoct_de_step(c, ds, prm, g, pop, fit, best, stream_id=stream, sample_idx=sidx)
+        np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32),
+                                      ref["pop_hist"][g].view(np.uint32), err_msg="generation %d" % g)
+        np.testing.assert_array_equal(fit.cpu().numpy(), ref["fit_hist"][g])
+    assert int(best.cpu()[0]) == ref["best"]
+
+
+def test_fit_subtree_matches_oracle(c):
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(0)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], 2)
+    ranks, nu = oracle.encode(w["X"])
+    ref = oracle.de_run(ranks, nu, w["y"], w["K"], depth=2, P=64, G=100, seed=0)
+    prm = deoct.make_params(2, 64, 100, seed=0)
+    import torch
+    pop = torch.empty((64, 6), dtype=torch.float32, device="cuda")
+    a, th, f = deoct.deoct_fit_subtree(c, ds, prm, pop_out=pop)
+    a_ref, th_ref = oracle.decode(ref["pop"][ref["best"]][None], 2, nu)
+    np.testing.assert_array_equal(a.astype(np.int32), a_ref[0])
+    np.testing.assert_array_equal(th, th_ref[0])
+    assert f == ref["fit"][ref["best"]]
+    np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), ref["pop"].view(np.uint32))
+
+
+def test_fit_subtree_with_seeds(c):
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(0, n=400)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], 4)
+    ranks, nu = oracle.encode(w["X"])
+    seeds = datagen.random_genes(5, 2, 8, _rng(3))
+    ref = oracle.de_run(ranks, nu, w["y"], w["K"], depth=2, P=16, G=12, seed=2, seeds=seeds)
+    prm = deoct.make_params(2, 16, 12, seed=2)
+    a, th, f = deoct.deoct_fit_subtree(c, ds, prm, seeds=to_dev(seeds))
+    assert f == ref["fit"][ref["best"]]
+
+
+def test_de_workload3_reduced_bit_exact(c):
+    """Large-scale DE shape (F=10, K=2, depth 4, P=1024, uint16 ranks) on 60k samples, 3 generations."""
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(3, n=60_000)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], 2)
+    ranks, nu = oracle.encode(w["X"])
+    ref = oracle.de_run(ranks, nu, w["y"], w["K"], depth=4, P=1024, G=3, seed=0)
+    prm = deoct.make_params(4, 1024, 3, seed=0)
+    import torch
+    pop = torch.empty((1024, 30), dtype=torch.float32, device="cuda")
+    a, th, f = deoct.deoct_fit_subtree(c, ds, prm, pop_out=pop)
+    np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), ref["pop"].view(np.uint32))
+    assert f == ref["fit"][ref["best"]]
+
+
+def test_invalid_arguments_are_rejected(c):
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(0, n=100)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], 2)
+    with pytest.raises(deoct.DeoctError) as e:
+        deoct.deoct_fit_subtree(c, ds, deoct.make_params(2, 3, 5))  # P < 4
+    assert e.value.code == deoct.DEOCT_ERR_INVALID
+    with pytest.raises(deoct.DeoctError):
+        deoct.deoct_fit_subtree(c, ds, deoct.make_params(11, 16, 5))  # depth > 10
+    # a tree naming a feature > F is reported, not read out of bounds
+    a = np.full((2, 3), 9, np.uint16)
+    th = np.zeros((2, 3), np.uint32)
+    deoct.deoct_eval_population(c, ds, to_dev(a), to_dev(th), 2)
+    with pytest.raises(deoct.DeoctError):
+        deoct.deoct_fit_subtree(c, ds, deoct.make_params(2, 16, 1))
+    # and the context recovers
+    deoct.deoct_fit_subtree(c, ds, deoct.make_params(2, 16, 1))
