@@ -118,6 +118,16 @@ DEOCT_API int deoct_set_timing(deoct_ctx* ctx, int enable);
 DEOCT_API int deoct_get_stats(deoct_ctx* ctx, deoct_stats* out);
 DEOCT_API int deoct_reset_stats(deoct_ctx* ctx);
 
+/* Override the evaluator's launch shape (0 keeps the library's choice):
+ *  S      samples per shared-memory tile (multiple of 128, 128..8192)
+ *  TG     trees per job (tree group), 1..4096
+ *  warps  warps per CTA, 1..16
+ *  grid   persistent CTAs (each walks an equal contiguous range of tiles)
+ * Results do not depend on the shape; only speed does.  Invalid values are
+ * DEOCT_ERR_INVALID; a shape whose tile does not fit in shared memory fails at
+ * the next evaluation. */
+DEOCT_API int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, int32_t grid);
+
 /* ---- a1: rank encoder ----------------------------------------------------
  * Section 3.1: the threshold set B_p of feature p is built from its sorted
  * unique values; a sample's position among them (its dense rank) decides every

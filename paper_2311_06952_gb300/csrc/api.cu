@@ -332,6 +332,22 @@ int deoct_reset_stats(deoct_ctx* ctx) {
   API_END
 }
 
+int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, int32_t grid) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  if (S != 0 && (S < 128 || S > 8192 || S % 128 != 0))
+    return set_error(DEOCT_ERR_INVALID, "S = %d: want a multiple of 128 in 128..8192", S);
+  if (TG < 0 || TG > kMaxPop) return set_error(DEOCT_ERR_INVALID, "TG = %d out of range", TG);
+  if (warps < 0 || warps > 16) return set_error(DEOCT_ERR_INVALID, "warps = %d out of range", warps);
+  if (grid < 0) return set_error(DEOCT_ERR_INVALID, "grid < 0");
+  ctx->force_S = S;
+  ctx->force_TG = TG;
+  ctx->force_warps = warps;
+  ctx->force_grid = grid;
+  return DEOCT_OK;
+  API_END
+}
+
 int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
                  void* ranks_out, int64_t ld, uint32_t* n_unique_out, void* stream) {
   API_BEGIN

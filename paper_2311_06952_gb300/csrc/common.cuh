@@ -90,8 +90,8 @@ struct deoct_ctx {
   std::vector<cudaEvent_t> ev_pairs;  // start/stop pairs of timed evaluator launches
   double eval_ms = 0.0;
   uint64_t eval_timed = 0;
-  // evaluator tile configuration chosen by the autotuner, keyed by shape
-  std::vector<std::pair<uint64_t, uint32_t>> tune_cache;
+  // evaluator launch shape forced by deoct_set_eval_config (0 = automatic)
+  int force_S = 0, force_TG = 0, force_warps = 0, force_grid = 0;
 };
 
 namespace deoct {

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
         }
       }
     }
+    jv.tile = nv.tile;  // the tile changes every iteration, the job only sometimes
     const EvalProb& P = *jv.p;
     const int64_t s0 = P.start + jv.tile * (int64_t)S;
     const int64_t rem = P.start + P.count - s0;
@@ -485,6 +486,10 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
   while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && (c.S > 256 || c.TG > 16)) {
     if (c.S > 256) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
   }
+  if (ctx->force_S) c.S = ctx->force_S;
+  if (ctx->force_TG) c.TG = std::min(ctx->force_TG, std::max(1, P));
+  if (ctx->force_warps) c.warps = ctx->force_warps;
+  if (ctx->force_grid) c.grid = ctx->force_grid;
   return c;
 }
 

@@ -30,7 +30,7 @@ EXPORTED = [
     "deoct_create", "deoct_destroy", "deoct_last_error_string", "deoct_version",
     "deoct_set_timing", "deoct_get_stats", "deoct_reset_stats", "deoct_encode",
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
-    "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search",
+    "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
 ]
 
 
@@ -84,6 +84,7 @@ def load(path: str | None = None):
             "deoct_set_timing": [_vp, ctypes.c_int],
             "deoct_get_stats": [_vp, ctypes.POINTER(Stats)],
             "deoct_reset_stats": [_vp],
+            "deoct_set_eval_config": [_vp, _i32, _i32, _i32, _i32],
             "deoct_encode": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp],
             "deoct_decode_population": [_vp, ctypes.POINTER(Dataset), _vp, _i32, _i32, _vp, _vp, _vp],
             "deoct_eval_population": [_vp, ctypes.POINTER(Dataset), _vp, _i64, _vp, _vp, _i32, _i32,
@@ -165,6 +166,10 @@ class Context:
 
     def reset_stats(self):
         _check(load().deoct_reset_stats(self.handle))
+
+    def set_eval_config(self, S=0, TG=0, warps=0, grid=0):
+        """Force the evaluator's launch shape (0 = automatic); results are unchanged."""
+        _check(load().deoct_set_eval_config(self.handle, S, TG, warps, grid))
 
 
 class DeviceDataset:

@@ -126,6 +126,33 @@ def test_eval_bit_exact(c, case):
     np.testing.assert_array_equal(u32(errors), ref_err)
 
 
+@pytest.mark.parametrize("shape", [(128, 3, 1, 1), (256, 16, 4, 3), (512, 64, 8, 7), (2048, 256, 16, 5),
+                                   (8192, 1, 2, 2)])
+def test_eval_launch_shapes_bit_exact(c, shape):
+    """Persistent CTAs walking many tiles and several tree groups give the same counts."""
+    from paper_2311_06952_gb300 import deoct
+    S, TG, warps, grid = shape
+    rng = _rng(200 + S)
+    n, F, K, depth, P = 23456, 6, 3, 3, 70
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+    try:
+        c.set_eval_config(S, TG, warps, grid)
+        for rb in (2, 4):
+            ds = gpu_dataset(c, X, y, K, rb)
+            counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+            np.testing.assert_array_equal(u32(counts), ref)
+            idx = rng.permutation(n)[: n // 2].astype(np.int32)
+            counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth,
+                                                    sample_idx=to_dev(idx))
+            np.testing.assert_array_equal(u32(counts), oracle.eval_counts(ranks, y, K, a, th, depth, idx=idx))
+    finally:
+        c.set_eval_config(0, 0, 0, 0)
+
+
 def test_eval_workload1_full_size(c):
     """Population-evaluation workload at its full size: n=1e5, F=20, K=3, 256 depth-3 trees."""
     from paper_2311_06952_gb300 import deoct
