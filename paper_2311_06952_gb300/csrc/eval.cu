@@ -365,6 +365,10 @@ int launch_t(deoct_ctx* ctx, const EvalArgs& args, const EvalConfig& cfg, size_t
     DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
   }
+  // all of the unified L1/shared array as shared memory, so that the occupancy
+  // computed below is the residency the launch gets
+  DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
   int grid = cfg.grid;
   if (grid <= 0) {
     int occ = 0;
