@@ -33,8 +33,7 @@ struct RankT<4> {
   typedef uint32_t T;
 };
 
-constexpr int kQMax = 4;  // ballot mode: bins per lane
-constexpr int kU = 2;     // chunks of 32 samples interleaved per warp
+constexpr int kQMax = 4;  // ballot mode: up to 4 bins per lane (2^D * K <= 128)
 
 struct EvalArgs {
   EvalProb single;
@@ -79,31 +78,145 @@ __device__ __forceinline__ void lookup_job(const EvalArgs& a, int64_t gt, JobVie
 
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
-// shared-memory layout shared by host sizing and the kernel
+// Shared-memory layout, shared by host sizing and the kernel:
+//   tile    [F][S] ranks in the compute layout (see tile_offset)
+//   stage   [F][S] TMA landing zone (uint16 only; the uint32 path lands in `tile`)
+//   nodes   [TG][B] {shared address of the feature row, theta}
+//   aux     ballot mode: class masks [S/32][Q][32]; atomic mode: labels [S]
+//   cnt     ballot mode: job counts [TG][2^D K]; atomic mode: per-warp histograms
 struct SmemLayout {
-  size_t tile, nodes, aux, cnt, total;
+  size_t tile, stage, nodes, aux, cnt, total;
 };
 __host__ __device__ __forceinline__ SmemLayout smem_layout(int mode, int W, int D, int S, int TG,
                                                            int Fmax, int Kmax, int warps) {
   const int B = (1 << D) - 1, L = 1 << D;
   const int LK = L * Kmax;
+  const size_t rows = align128((size_t)Fmax * S * W);
   SmemLayout s;
   s.tile = 0;
-  s.nodes = align128((size_t)Fmax * S * W);
+  s.stage = rows;
+  s.nodes = s.stage + (W == 2 ? rows : 0);
+  s.aux = s.nodes + align128((size_t)TG * B * 8);
   if (mode == 0) {
     const int Q = (LK + 31) / 32;
-    s.aux = s.nodes + align128((size_t)TG * B * 8);
     s.cnt = s.aux + align128((size_t)S * Q * 4);
     s.total = s.cnt + align128((size_t)TG * LK * 4);
   } else {
-    s.aux = s.nodes + align128((size_t)TG * B * 8);  // labels [S]
-    s.cnt = s.aux + align128((size_t)S);             // per-warp histograms
+    s.cnt = s.aux + align128((size_t)S);
     s.total = s.cnt + align128((size_t)warps * LK * 4);
   }
   return s;
 }
 
-template <int W, int D, int MODE>
+// Byte offset of sample j inside a feature row of the compute tile.  uint32
+// ranks: natural order (lane l of a warp reads bank l).  uint16 ranks: the two
+// chunks of 32 samples of a chunk pair share 32-bit words -- word l of pair p
+// holds sample 64p+l (low half) and 64p+32+l (high half) -- so a warp reading
+// one chunk touches 32 distinct banks whatever rows its lanes are on.
+template <int W>
+__device__ __forceinline__ uint32_t tile_offset(uint32_t j) {
+  if (W == 4) return j * 4u;
+  return (j >> 6) * 128u + (j & 31u) * 4u + ((j >> 5) & 1u) * 2u;
+}
+// offset between the two chunks of a pair for the same lane
+template <int W>
+struct PairGeom {
+  static constexpr uint32_t kSecond = (W == 2) ? 2u : 128u;
+  static constexpr uint32_t kPairStride = 64u * W;
+};
+
+template <int W>
+__device__ __forceinline__ uint32_t lds_rank(uint32_t addr) {
+  uint32_t v;
+  if (W == 2) {
+    unsigned short h;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(addr));
+    v = h;
+  } else {
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  }
+  return v;
+}
+__device__ __forceinline__ uint2 lds_node(uint32_t addr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+// Route 64 samples (the two chunks of pair p) of one tree and add the bin
+// counts owned by this lane.  Ballot of level d = "went right" at depth d for
+// the 32 samples of a chunk; bin b = leaf*K + k is owned by lane b % 32.
+template <int W, int D, int Q>
+__device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
+                                           uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
+                                           uint32_t tnb48, uint32_t ntnb, uint32_t ymA, uint32_t ymB,
+                                           const uint32_t (&cst)[Q][D], uint32_t (&cnt)[Q]) {
+  constexpr uint32_t SEC = PairGeom<W>::kSecond;
+  uint32_t BA[D], BB[D];
+  // level 0: the root is the same node for every lane
+  const uint32_t ra0 = lds_rank<W>(row0 + jb);
+  const uint32_t rb0 = lds_rank<W>(row0 + jb + SEC);
+  const bool pa0 = ra0 >= th0, pb0 = rb0 >= th0;
+  BA[0] = __ballot_sync(0xFFFFFFFFu, pa0);
+  BB[0] = __ballot_sync(0xFFFFFFFFu, pb0);
+  if (D >= 2) {
+    // level 1: two candidate nodes held in registers
+    const uint32_t rowa = pa0 ? row3 : row2, tha = pa0 ? th3 : th2;
+    const uint32_t rowb = pb0 ? row3 : row2, thb = pb0 ? th3 : th2;
+    const uint32_t ra1 = lds_rank<W>(rowa + jb);
+    const uint32_t rb1 = lds_rank<W>(rowb + jb + SEC);
+    const bool pa1 = ra1 >= tha, pb1 = rb1 >= thb;
+    BA[1 < D ? 1 : 0] = __ballot_sync(0xFFFFFFFFu, pa1);
+    BB[1 < D ? 1 : 0] = __ballot_sync(0xFFFFFFFFu, pb1);
+    // shared address of node t = 4 + 2 p0 + p1
+    uint32_t aa = (pa0 ? tnb48 : tnb32) + (pa1 ? 8u : 0u);
+    uint32_t ab = (pb0 ? tnb48 : tnb32) + (pb1 ? 8u : 0u);
+#pragma unroll
+    for (int d = 2; d < D; ++d) {
+      const uint2 na = lds_node(aa);
+      const uint2 nb = lds_node(ab);
+      const uint32_t ra = lds_rank<W>(na.x + jb);
+      const uint32_t rb = lds_rank<W>(nb.x + jb + SEC);
+      const bool pa = ra >= na.y, pb = rb >= nb.y;
+      BA[d] = __ballot_sync(0xFFFFFFFFu, pa);
+      BB[d] = __ballot_sync(0xFFFFFFFFu, pb);
+      if (d + 1 < D) {  // node 2t + p: address 2 addr(t) - base + 8 p
+        aa = 2u * aa + ntnb + (pa ? 8u : 0u);
+        ab = 2u * ab + ntnb + (pb ? 8u : 0u);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    uint32_t ma = lds_u32(ymA + q * 128u);
+    uint32_t mb = lds_u32(ymB + q * 128u);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      ma &= BA[d] ^ cst[q][d];
+      mb &= BB[d] ^ cst[q][d];
+    }
+    cnt[q] += __popc(ma) + __popc(mb);
+  }
+}
+
+// Stage the rank rows of one tile.  TMA path: one elected thread issues a 1-D
+// bulk copy per feature row into `dst` and arms the mbarrier.
+__device__ __forceinline__ void issue_tile_tma(const EvalProb& P, int64_t s0, int ns, int S, int W,
+                                               unsigned char* dst, uint64_t* bar) {
+  fence_proxy_async_smem();
+  const uint32_t bytes = ((uint32_t)ns * W + 15u) & ~15u;
+  mbar_arrive_expect_tx(bar, bytes * (uint32_t)P.F);
+  const unsigned char* src = static_cast<const unsigned char*>(P.ranks);
+  for (int f = 0; f < P.F; ++f)
+    bulk_g2s(dst + (size_t)f * S * W, src + ((int64_t)f * P.ld + s0) * W, bytes, bar);
+}
+
+template <int W, int D, int MODE, int Q>
 __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   constexpr int B = (1 << D) - 1;
   constexpr int L = 1 << D;
@@ -117,10 +230,14 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   const int nw = blockDim.x >> 5;
   const SmemLayout lay = smem_layout(MODE, W, D, S, a.TG, a.Fmax, a.Kmax, nw);
   unsigned char* tileb = smem + lay.tile;
+  unsigned char* stageb = (W == 2) ? smem + lay.stage : tileb;
   uint2* nodes_s = reinterpret_cast<uint2*>(smem + lay.nodes);
   uint32_t* aux32 = reinterpret_cast<uint32_t*>(smem + lay.aux);
   uint8_t* lab_s = smem + lay.aux;
   uint32_t* cnt_s = reinterpret_cast<uint32_t*>(smem + lay.cnt);
+  const uint32_t tile_sa = smem_u32(tileb);
+  const uint32_t nodes_sa = smem_u32(nodes_s);
+  const uint32_t aux_sa = smem_u32(aux32);
 
   const int64_t T = a.total_tiles;
   const int64_t t0 = (int64_t)blockIdx.x * T / gridDim.x;
@@ -140,10 +257,9 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   uint32_t phase = 0;
   int cur_job = -1;
   JobView jv;
-  int K = 0, LK = 0, Q = 0;
-  // ballot mode per-lane constants: for bin b = lane + 32q, the mask that
-  // selects "went right" (bit set) or "went left" at level d
-  uint32_t cst[kQMax][D];
+  int K = 0, LK = 0;
+  uint32_t cst[Q][D];  // ballot mode: per owned bin, "right" (0) or "left" (~0) at level d
+  bool staged = false; // the current tile's rows are already in flight (prefetched)
 
   auto flush = [&](const JobView& v) {
     if (MODE == 0) {
@@ -165,18 +281,17 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
       cur_job = nv.job;
       K = jv.p->K;
       LK = L * K;
-      Q = (LK + 31) >> 5;
-      // nodes of the job's trees -> {byte offset of the feature row in the tile, theta}
+      // nodes -> {shared address of the feature row in the tile, theta}
       const uint32_t* gn = jv.p->nodes + (int64_t)jv.tree0 * B;
       for (int e = threadIdx.x; e < jv.ntrees * B; e += blockDim.x) {
         uint32_t pk = gn[e];
         uint32_t f = pk >> 24;
-        nodes_s[e] = make_uint2(f * (uint32_t)S * (uint32_t)W, pk & kThetaMask);
+        nodes_s[e] = make_uint2(tile_sa + f * (uint32_t)S * (uint32_t)W, pk & kThetaMask);
       }
       if (MODE == 0) {
         for (int e = threadIdx.x; e < jv.ntrees * LK; e += blockDim.x) cnt_s[e] = 0;
 #pragma unroll
-        for (int q = 0; q < kQMax; ++q) {
+        for (int q = 0; q < Q; ++q) {
           int b = lane + 32 * q;
           int leaf = (b < LK) ? b / K : 0;
 #pragma unroll
@@ -191,21 +306,14 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     const int64_t rem = P.start + P.count - s0;
     const int ns = rem < S ? (int)rem : S;
     const int nch = (ns + 31) >> 5;
-    const int nchU = (nch + kU - 1) / kU * kU;
+    const int npair = (nch + 1) >> 1;
 
     // ---- stage rank rows -------------------------------------------------
     if (P.tma) {
-      if (threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        const uint32_t bytes = ((uint32_t)ns * W + 15u) & ~15u;
-        mbar_arrive_expect_tx(&mbar, bytes * (uint32_t)P.F);
-        const unsigned char* src = static_cast<const unsigned char*>(P.ranks);
-        for (int f = 0; f < P.F; ++f)
-          bulk_g2s(tileb + (size_t)f * S * W, src + ((int64_t)f * P.ld + s0) * W, bytes, &mbar);
-      }
+      if (!staged && threadIdx.x == 0) issue_tile_tma(P, s0, ns, S, W, stageb, &mbar);
     } else {
-      const RT* src = static_cast<const RT*>(P.ranks);
       RT* dst = reinterpret_cast<RT*>(tileb);
+      const RT* src = static_cast<const RT*>(P.ranks);
       for (int e = threadIdx.x; e < P.F * S; e += blockDim.x) {
         int f = e / S, j = e - f * S;
         if (j < ns) {
@@ -214,13 +322,16 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
             atomicOr(a.status, ST_BAD_INDEX);
             col = 0;
           }
-          dst[e] = src[(int64_t)f * P.ld + col];
+          *reinterpret_cast<RT*>(tileb + (size_t)f * S * W + tile_offset<W>((uint32_t)j)) =
+              src[(int64_t)f * P.ld + col];
         }
       }
+      (void)dst;
     }
+    staged = false;
     // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
     if (MODE == 0) {
-      for (int c = warp; c < nchU; c += nw) {
+      for (int c = warp; c < 2 * npair; c += nw) {
         int j = c * 32 + lane;
         uint32_t y = 0xFFu;
         if (j < ns) {
@@ -228,21 +339,22 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
           if ((uint64_t)col >= (uint64_t)P.ncols) col = 0;
           y = P.labels[col];
         }
-        uint32_t mine[kQMax] = {0u, 0u, 0u, 0u};
+        uint32_t mine[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) mine[q] = 0u;
         for (int k = 0; k < K; ++k) {
           uint32_t m = __ballot_sync(0xFFFFFFFFu, y == (uint32_t)k);
 #pragma unroll
-          for (int q = 0; q < kQMax; ++q) {
+          for (int q = 0; q < Q; ++q) {
             int b = lane + 32 * q;
             if (b < LK && (b % K) == k) mine[q] = m;
           }
         }
 #pragma unroll
-        for (int q = 0; q < kQMax; ++q)
-          if (q < Q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+        for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
       }
     } else {
-      for (int j = threadIdx.x; j < nchU * 32; j += blockDim.x) {
+      for (int j = threadIdx.x; j < 2 * npair * 32; j += blockDim.x) {
         uint8_t y = 0xFF;
         if (j < ns) {
           int64_t col = P.idx ? (int64_t)P.idx[s0 + j] : s0 + j;
@@ -252,89 +364,83 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
         lab_s[j] = y;
       }
     }
-    int ok = 1;
-    if (P.tma) ok = mbar_wait_bounded(&mbar, phase, a.status) ? 1 : 0;
-    phase ^= (P.tma ? 1u : 0u);
-    if (__syncthreads_or(!ok)) {
-      // timed out (status recorded): give the copies in flight one more bounded
-      // wait before the CTA leaves
-      if (threadIdx.x == 0) mbar_wait_bounded(&mbar, phase ^ 1u, a.status);
+    if (P.tma) {
+      int ok = mbar_wait_bounded(&mbar, phase, a.status) ? 1 : 0;
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        // timed out (status recorded): give the copies in flight one more
+        // bounded wait before the CTA leaves
+        if (threadIdx.x == 0) mbar_wait_bounded(&mbar, phase ^ 1u, a.status);
+        __syncthreads();
+        return;
+      }
+      if (W == 2) {
+        // stage (natural order) -> tile (chunk-pair interleaved)
+        const uint16_t* st = reinterpret_cast<const uint16_t*>(stageb);
+        uint32_t* tw = reinterpret_cast<uint32_t*>(tileb);
+        const int words = npair * 32;  // per row
+        for (int e = threadIdx.x; e < P.F * words; e += blockDim.x) {
+          int f = e / words, w = e - f * words;
+          int pp = w >> 5, l = w & 31;
+          const uint16_t* srow = st + (size_t)f * S + pp * 64 + l;
+          tw[(size_t)f * (S / 2) + w] = (uint32_t)srow[0] | ((uint32_t)srow[32] << 16);
+        }
+        __syncthreads();
+        // prefetch the next tile of this CTA into the free landing zone
+        if (gt + 1 < t1) {
+          JobView xv;
+          lookup_job(a, gt + 1, &xv);
+          const EvalProb& X = *xv.p;
+          if (X.tma) {
+            if (threadIdx.x == 0) {
+              const int64_t xs0 = X.start + xv.tile * (int64_t)S;
+              const int64_t xrem = X.start + X.count - xs0;
+              issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, &mbar);
+            }
+            staged = true;
+          }
+        }
+      }
+    } else {
       __syncthreads();
-      return;
     }
 
     // ---- route + count ---------------------------------------------------
-    const unsigned char* tb = tileb;
     for (int i = warp; i < jv.ntrees; i += nw) {
-      const uint2* tn = nodes_s + i * B - 1;  // tn[t] = node t (1-based)
-      const uint2 n1 = tn[1];
-      uint2 n2 = n1, n3 = n1;
-      if (D >= 2) {
-        n2 = tn[2];
-        n3 = tn[3];
-      }
+      const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
+      const uint2 n1 = nodes_s[i * B];
       if (MODE == 0) {
-        uint32_t cnt[kQMax] = {0u, 0u, 0u, 0u};
-        for (int c = 0; c < nchU; c += kU) {
-          uint32_t bal[kU][D];
-          uint32_t t[kU];
-          const uint32_t jb0 = (uint32_t)(c * 32 + lane) * W;
+        uint2 n2 = n1, n3 = n1;
+        if (D >= 2) {
+          n2 = nodes_s[i * B + 1];
+          n3 = nodes_s[i * B + 2];
+        }
+        uint32_t cnt[Q];
 #pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const uint32_t jb = jb0 + u * 32 * W;
-            uint32_t rv = *reinterpret_cast<const RT*>(tb + n1.x + jb);
-            uint32_t g = rv >= n1.y;
-            bal[u][0] = __ballot_sync(0xFFFFFFFFu, g);
-            t[u] = 2 + g;
-            if (D >= 2) {
-              uint32_t ro = g ? n3.x : n2.x;
-              uint32_t th = g ? n3.y : n2.y;
-              uint32_t rv1 = *reinterpret_cast<const RT*>(tb + ro + jb);
-              uint32_t g1 = rv1 >= th;
-              bal[u][1 < D ? 1 : 0] = __ballot_sync(0xFFFFFFFFu, g1);
-              t[u] = 2 * t[u] + g1;
-            }
-          }
-#pragma unroll
-          for (int d = 2; d < D; ++d) {
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const uint32_t jb = jb0 + u * 32 * W;
-              const uint2 nd = tn[t[u]];
-              uint32_t rv = *reinterpret_cast<const RT*>(tb + nd.x + jb);
-              uint32_t g = rv >= nd.y;
-              bal[u][d] = __ballot_sync(0xFFFFFFFFu, g);
-              t[u] = 2 * t[u] + g;
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-#pragma unroll
-            for (int q = 0; q < kQMax; ++q) {
-              if (q < Q) {
-                uint32_t m = aux32[((c + u) * Q + q) * 32 + lane];
-#pragma unroll
-                for (int d = 0; d < D; ++d) m &= bal[u][d] ^ cst[q][d];
-                cnt[q] += __popc(m);
-              }
-            }
-          }
+        for (int q = 0; q < Q; ++q) cnt[q] = 0u;
+        const uint32_t ntnb = 0u - tnb;
+        for (int pp = 0; pp < npair; ++pp) {
+          const uint32_t jb = (uint32_t)pp * PairGeom<W>::kPairStride + (uint32_t)lane * 4u;
+          const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
+          const uint32_t ymB = ymA + Q * 128u;
+          route_pair<W, D, Q>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u, tnb + 48u, ntnb,
+                              ymA, ymB, cst, cnt);
         }
 #pragma unroll
-        for (int q = 0; q < kQMax; ++q) {
+        for (int q = 0; q < Q; ++q) {
           int b = lane + 32 * q;
-          if (q < Q && b < LK) cnt_s[i * LK + b] += cnt[q];
+          if (b < LK) cnt_s[i * LK + b] += cnt[q];
         }
       } else {
         uint32_t* hw = cnt_s + warp * (L * a.Kmax);
         for (int c = 0; c < nch; ++c) {
           const uint32_t j = (uint32_t)(c * 32 + lane);
-          const uint32_t jb = j * W;
+          const uint32_t jo = tile_offset<W>(j);
           uint32_t t = 1;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            const uint2 nd = tn[t];
-            uint32_t rv = *reinterpret_cast<const RT*>(tb + nd.x + jb);
+            const uint2 nd = lds_node(tnb + 8u * t);
+            uint32_t rv = lds_rank<W>(nd.x + jo);
             t = 2 * t + (rv >= nd.y ? 1u : 0u);
           }
           uint32_t y = lab_s[j];
@@ -354,13 +460,14 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     }
     __syncthreads();
   }
+  if (staged && threadIdx.x == 0) mbar_wait_bounded(&mbar, phase, a.status);  // never left in flight
   if (cur_job >= 0) flush(jv);
 }
 
-template <int W, int D, int MODE>
+template <int W, int D, int MODE, int Q>
 int launch_t(deoct_ctx* ctx, const EvalArgs& args, const EvalConfig& cfg, size_t smem,
              cudaStream_t s) {
-  auto kern = eval_kernel<W, D, MODE>;
+  auto kern = eval_kernel<W, D, MODE, Q>;
   if (smem > 48 * 1024) {
     DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
@@ -385,26 +492,31 @@ int launch_t(deoct_ctx* ctx, const EvalArgs& args, const EvalConfig& cfg, size_t
 }
 
 template <int W, int D>
-int dispatch_mode(deoct_ctx* ctx, int mode, const EvalArgs& args, const EvalConfig& cfg,
+int dispatch_mode(deoct_ctx* ctx, int mode, int Q, const EvalArgs& args, const EvalConfig& cfg,
                   size_t smem, cudaStream_t s) {
-  if (mode == 0) return launch_t<W, D, 0>(ctx, args, cfg, smem, s);
-  return launch_t<W, D, 1>(ctx, args, cfg, smem, s);
+  if (mode == 1) return launch_t<W, D, 1, 1>(ctx, args, cfg, smem, s);
+  switch (Q) {
+    case 1: return launch_t<W, D, 0, 1>(ctx, args, cfg, smem, s);
+    case 2: return launch_t<W, D, 0, 2>(ctx, args, cfg, smem, s);
+    case 3: return launch_t<W, D, 0, 3>(ctx, args, cfg, smem, s);
+    default: return launch_t<W, D, 0, 4>(ctx, args, cfg, smem, s);
+  }
 }
 
 template <int W>
-int dispatch_depth(deoct_ctx* ctx, int D, int mode, const EvalArgs& args, const EvalConfig& cfg,
-                   size_t smem, cudaStream_t s) {
+int dispatch_depth(deoct_ctx* ctx, int D, int mode, int Q, const EvalArgs& args,
+                   const EvalConfig& cfg, size_t smem, cudaStream_t s) {
   switch (D) {
-    case 1: return dispatch_mode<W, 1>(ctx, mode, args, cfg, smem, s);
-    case 2: return dispatch_mode<W, 2>(ctx, mode, args, cfg, smem, s);
-    case 3: return dispatch_mode<W, 3>(ctx, mode, args, cfg, smem, s);
-    case 4: return dispatch_mode<W, 4>(ctx, mode, args, cfg, smem, s);
-    case 5: return dispatch_mode<W, 5>(ctx, mode, args, cfg, smem, s);
-    case 6: return launch_t<W, 6, 1>(ctx, args, cfg, smem, s);
-    case 7: return launch_t<W, 7, 1>(ctx, args, cfg, smem, s);
-    case 8: return launch_t<W, 8, 1>(ctx, args, cfg, smem, s);
-    case 9: return launch_t<W, 9, 1>(ctx, args, cfg, smem, s);
-    case 10: return launch_t<W, 10, 1>(ctx, args, cfg, smem, s);
+    case 1: return dispatch_mode<W, 1>(ctx, mode, Q, args, cfg, smem, s);
+    case 2: return dispatch_mode<W, 2>(ctx, mode, Q, args, cfg, smem, s);
+    case 3: return dispatch_mode<W, 3>(ctx, mode, Q, args, cfg, smem, s);
+    case 4: return dispatch_mode<W, 4>(ctx, mode, Q, args, cfg, smem, s);
+    case 5: return dispatch_mode<W, 5>(ctx, mode, Q, args, cfg, smem, s);
+    case 6: return launch_t<W, 6, 1, 1>(ctx, args, cfg, smem, s);
+    case 7: return launch_t<W, 7, 1, 1>(ctx, args, cfg, smem, s);
+    case 8: return launch_t<W, 8, 1, 1>(ctx, args, cfg, smem, s);
+    case 9: return launch_t<W, 9, 1, 1>(ctx, args, cfg, smem, s);
+    case 10: return launch_t<W, 10, 1, 1>(ctx, args, cfg, smem, s);
   }
   return set_error(DEOCT_ERR_INVALID, "depth %d outside 1..%d", D, kMaxDepth);
 }
@@ -526,8 +638,9 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
     DEOCT_CUDA_TRY(cudaEventCreate(&e1));
     DEOCT_CUDA_TRY(cudaEventRecord(e0, stream));
   }
-  int rc = (W == 2) ? dispatch_depth<2>(ctx, D, mode, a, cfg, smem, stream)
-                    : dispatch_depth<4>(ctx, D, mode, a, cfg, smem, stream);
+  const int Q = ((1 << D) * plan.Kmax + 31) / 32;
+  int rc = (W == 2) ? dispatch_depth<2>(ctx, D, mode, Q, a, cfg, smem, stream)
+                    : dispatch_depth<4>(ctx, D, mode, Q, a, cfg, smem, stream);
   if (rc != DEOCT_OK) return rc;
   ctx->eval_launches += 1;
   if (ctx->timing) {
