@@ -263,6 +263,8 @@ int deoct_create(deoct_ctx** out, int device) {
   DEOCT_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
   DEOCT_CUDA_TRY(
       cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  DEOCT_CUDA_TRY(
+      cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   cudaError_t e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e != cudaSuccess) {
     delete ctx;
@@ -282,6 +284,7 @@ int deoct_destroy(deoct_ctx* ctx) {
   for (int i = 0; i < SL_COUNT; ++i)
     if (ctx->scratch[i].ptr) cudaFree(ctx->scratch[i].ptr);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   for (cudaEvent_t ev : ctx->ev_pairs) cudaEventDestroy(ev);
   delete ctx;
@@ -490,6 +493,38 @@ int deoct_fit_subtree(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sa
   memcpy(theta_out, h + 8, B * 4);
   memcpy(a_out, h + 8 + B * 4, B * 2);
   return DEOCT_OK;
+  API_END
+}
+
+int deoct_fit_moving_horizon(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* params,
+                             uint16_t* a_out, uint32_t* theta_out, uint8_t* leaf_class_out,
+                             int32_t* kind_out, double* node_fit_out, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  DEOCT_TRY(validate_dataset(ds));
+  DEOCT_TRY(validate_params(params, false));
+  if (params->horizon < 1) return set_error(DEOCT_ERR_INVALID, "horizon must be >= 1");
+  const bool needs_de = params->horizon >= 2 && params->depth >= 2;
+  if (needs_de && (params->pop < kMinPop || params->pop > kMaxPop))
+    return set_error(DEOCT_ERR_INVALID, "population %d outside %d..%d", params->pop, kMinPop, kMaxPop);
+  if (!a_out || !theta_out || !leaf_class_out) return set_error(DEOCT_ERR_INVALID, "NULL host output");
+  return mh_run(ctx, ds, params, a_out, theta_out, leaf_class_out, kind_out, node_fit_out,
+                static_cast<cudaStream_t>(stream));
+  API_END
+}
+
+int deoct_depth1_search(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
+                        int64_t n_sub, int32_t n_min, double alpha, uint16_t* a_out,
+                        uint32_t* theta_out, double* fitness_out, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  DEOCT_TRY(validate_dataset(ds));
+  DEOCT_TRY(validate_subset(ds, sample_idx, n_sub));
+  if (n_min < 0) return set_error(DEOCT_ERR_INVALID, "n_min < 0");
+  if (!(alpha == alpha)) return set_error(DEOCT_ERR_INVALID, "alpha is NaN");
+  if (!a_out || !theta_out || !fitness_out) return set_error(DEOCT_ERR_INVALID, "NULL host output");
+  return depth1_run(ctx, ds, sample_idx, n_sub, n_min, alpha, a_out, theta_out, fitness_out,
+                    static_cast<cudaStream_t>(stream));
   API_END
 }
 

@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <array>
 #include <string>
 #include <vector>
 
@@ -78,6 +79,8 @@ struct deoct_ctx {
   int device = 0;
   int num_sms = 0;
   int max_smem_optin = 0;
+  int smem_per_sm = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
   int* d_status = nullptr;  // device status word (bits ST_*)
   deoct::Scratch scratch[deoct::SL_COUNT];
   // pinned host staging for small read-backs
@@ -90,6 +93,8 @@ struct deoct_ctx {
   std::vector<cudaEvent_t> ev_pairs;  // start/stop pairs of timed evaluator launches
   double eval_ms = 0.0;
   uint64_t eval_timed = 0;
+  // evaluator shapes picked by the autotuner, keyed by workload class
+  std::vector<std::pair<uint64_t, std::array<int, 3>>> tuned;
   // evaluator launch shape forced by deoct_set_eval_config (0 = automatic)
   int force_S = 0, force_TG = 0, force_warps = 0, force_grid = 0;
 };

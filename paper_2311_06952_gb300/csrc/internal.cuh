@@ -123,4 +123,14 @@ int radix_sort_segments(deoct_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1
                         int64_t n, int F, int bits, uint32_t** keys_out, uint32_t** vals_out,
                         cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// moving horizon (mh.cu)
+// ---------------------------------------------------------------------------
+int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uint16_t* a_out,
+           uint32_t* th_out, uint8_t* leaf_class_out, int32_t* kind_out, double* node_fit_out,
+           cudaStream_t s);
+int depth1_run(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx, int64_t n_sub,
+               int n_min, double alpha, uint16_t* a_out, uint32_t* th_out, double* f_out,
+               cudaStream_t s);
+
 }  // namespace deoct
