@@ -104,34 +104,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _dist_setup(gpus):
+def _dist_setup():
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    from paper_2311_06952_gb300 import multirank
+    rank, world, local = multirank.env_ranks()
+    torch.cuda.set_device(local if world > 1 else 0)
+    multirank.init("nccl", world)
     return rank, world, local
-
-
-def _barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def _max_over_ranks(x, world):
-    if world <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
 
 
 def _cpu_baseline(w, budget_s=12.0):
@@ -196,10 +175,11 @@ def run_ours(args):
     from paper_2311_06952_gb300 import build as _build
     from paper_2311_06952_gb300 import datagen, deoct
 
-    rank, world, local = _dist_setup(args.gpus)
-    if rank == 0 or world > 1:
+    from paper_2311_06952_gb300 import multirank
+    rank, world, local = _dist_setup()
+    if rank == 0:
         _build.build()
-    _barrier(world)
+    multirank.barrier(world)
     w = dict(WORKLOAD)
     data = datagen.make_workload(3, n=args.n)
     n, F, K = data["X"].shape[0], data["X"].shape[1], data["K"]
@@ -219,30 +199,30 @@ def run_ours(args):
         return deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)
 
     for i in range(args.warmup):
-        step(rank)
+        step(multirank.stream_id(rank))
     torch.cuda.synchronize()
     ctx.reset_stats()
     ctx.set_timing(True)
     clk = ClockSampler(local) if rank == 0 else None
     if clk:
         clk.start()
-    _barrier(world)
+    multirank.barrier(world)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        res = step(rank)
+        res = step(multirank.stream_id(rank))
     e1.record(stream)
     torch.cuda.synchronize()
-    _barrier(world)
+    multirank.barrier(world)
     ms_total = e0.elapsed_time(e1)
     clocks = clk.stop() if clk else None
     st = ctx.stats()
     ctx.set_timing(False)
-    ms_total = _max_over_ranks(ms_total, world)
+    ms_total = multirank.max_over_ranks(ms_total, world, "cuda")
     ms_step = ms_total / args.steps
-    value = evals_per_step * world / (ms_step / 1000.0)
+    value = multirank.whole_job_rate(evals_per_step, world, ms_step / 1000.0)
 
     # ---- end to end through the public API, host buffers ----------------------
     Xh = torch.from_numpy(data["X"]).pin_memory()
@@ -258,15 +238,15 @@ def run_ours(args):
         ds = deoct.DeviceDataset(r_, 2, nu_, yg, n, F, K)
         return deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)  # host outputs (sync)
 
-    e2e_step(rank)
-    _barrier(world)
+    e2e_step(multirank.stream_id(rank))
+    multirank.barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        e2e_step(rank)
+        e2e_step(multirank.stream_id(rank))
     torch.cuda.synchronize()
-    t_e2e = _max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = evals_per_step * world / (t_e2e / args.steps)
+    t_e2e = multirank.max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_value = multirank.whole_job_rate(evals_per_step, world, t_e2e / args.steps)
 
     if rank != 0:
         return 0

@@ -311,3 +311,4 @@ def deoct_depth1_search(ctx: Context, ds: DeviceDataset, sample_idx=None, n_min=
                                       alpha, ctypes.byref(a), ctypes.byref(th), ctypes.byref(f),
                                       _stream(stream)))
     return a.value, th.value, f.value
+
