@@ -236,6 +236,34 @@ DEOCT_API int deoct_depth1_search(deoct_ctx* ctx, const deoct_dataset* ds, const
                         int64_t n_sub, int32_t n_min, double alpha, uint16_t* a_out,
                         uint32_t* theta_out, double* fitness_out, void* stream);
 
+/* ---- evaluation without device allocation --------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory -- a host framework that owns all device memory
+ * through its own pool, or code that must not take the device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause.  It computes exactly
+ * what deoct_eval_population computes, but needs no deoct_ctx and calls no
+ * allocator: its scratch (packed trees, a status word, and the class counts
+ * when counts_out is NULL) is one fixed array of DEOCT_NOALLOC_SCRATCH_BYTES
+ * bytes inside the library, resident on every GPU that loads the library until
+ * the process exits.
+ *  - Runs on the current CUDA device.  The first call on a device looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call before
+ *    any stream capture.
+ *  - Requests needing more scratch than the array holds (P * (2^depth - 1) * 4
+ *    bytes of trees, plus P * 2^depth * K * 4 bytes of counts when counts_out is
+ *    NULL, plus 256) return DEOCT_ERR_INVALID before any GPU work.
+ *  - Every call shares the one array and each call clears what must start at
+ *    zero; calls whose GPU work overlaps (other streams, other threads) race on
+ *    it and must be serialised by the caller.
+ *  - Trees naming a feature > F route right; with no context there is no later
+ *    sync call to report it.
+ * Arguments as deoct_eval_population.  async. */
+#define DEOCT_NOALLOC_SCRATCH_BYTES (8u << 20)
+DEOCT_API int deoct_eval_population_noalloc(const deoct_dataset* ds, const int32_t* sample_idx,
+                                            int64_t n_sub, const uint16_t* a, const uint32_t* theta,
+                                            int32_t P, int32_t depth, uint32_t* counts_out,
+                                            uint32_t* errors_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

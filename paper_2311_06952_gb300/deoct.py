@@ -31,7 +31,9 @@ EXPORTED = [
     "deoct_set_timing", "deoct_get_stats", "deoct_reset_stats", "deoct_encode",
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
     "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
+    "deoct_eval_population_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class DeoctError(RuntimeError):
@@ -99,6 +101,8 @@ def load(path: str | None = None):
                                          _vp, _vp, _vp, _vp],
             "deoct_depth1_search": [_vp, ctypes.POINTER(Dataset), _vp, _i64, _i32, ctypes.c_double,
                                     _vp, _vp, _vp, _vp],
+            "deoct_eval_population_noalloc": [ctypes.POINTER(Dataset), _vp, _i64, _vp, _vp, _i32, _i32,
+                                              _vp, _vp, _vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -312,3 +316,16 @@ def deoct_depth1_search(ctx: Context, ds: DeviceDataset, sample_idx=None, n_min=
                                       _stream(stream)))
     return a.value, th.value, f.value
 
+
+def deoct_eval_population_noalloc(ds: DeviceDataset, a, theta, depth: int, counts_out, errors_out,
+                                  sample_idx=None, stream=None):
+    """The evaluator without any device allocation (no context; fixed library
+    scratch).  The caller passes every output buffer; counts_out may be None, in
+    which case the counts stay in the library's scratch.  Runs on the current
+    device; calls whose GPU work overlaps must be serialised by the caller."""
+    P = a.shape[0]
+    n_sub = ds.n if sample_idx is None else sample_idx.numel()
+    _check(load().deoct_eval_population_noalloc(ctypes.byref(ds.c), _ptr(sample_idx), n_sub, _ptr(a),
+                                                _ptr(theta), P, depth, _ptr(counts_out), _ptr(errors_out),
+                                                _stream(stream)))
+    return counts_out, errors_out
