@@ -169,6 +169,62 @@ def run_reference(args):
     return 0
 
 
+MH_WORKLOAD = ("mh-batched: n=1e6, F=30 (15 U(0,1) + 15 LogNormal(0,1)), K=4 planted depth-6 tree 5% "
+               "flips, uint32 ranks; moving-horizon D=8, horizon 3, P=128, G=200, M=0.5, CR=0.9")
+
+
+def _mh_node_counts(ranks_np, a, th, D):
+    """Samples reaching each node of a fitted tree (host routing, for the work count)."""
+    n = ranks_np.shape[1]
+    node = np.ones(n, np.int64)
+    counts = np.zeros(1 << (D + 1), np.int64)
+    for d in range(D):
+        cnt = np.bincount(node, minlength=1 << (D + 1))
+        counts[1 << d: 1 << (d + 1)] = cnt[1 << d: 1 << (d + 1)]
+        at = a[node - 1].astype(np.int64)
+        tt = th[node - 1].astype(np.int64)
+        rk = ranks_np[np.maximum(at - 1, 0), np.arange(n)].astype(np.int64)
+        node = np.where((at > 0) & (rk < tt), 2 * node, 2 * node + 1)
+    return counts
+
+
+def mh_compare(args):
+    """Moving-horizon training, batched level solve vs plain per-node launches, same GPU."""
+    import torch
+    from paper_2311_06952_gb300 import datagen, deoct
+    w = datagen.make_workload(2, n=args.mh_n)
+    ctx = deoct.Context(torch.cuda.current_device())
+    ds = deoct.encode_dataset(ctx, torch.from_numpy(w["X"]).cuda(), torch.from_numpy(w["y"]).cuda(),
+                              w["K"], 4)
+    res = {}
+    for name, flags in (("batched", deoct.DEOCT_BATCHED), ("plain", 0)):
+        prm = deoct.make_params(w["depth"], w["P"], w["G"], mut_f=w["M"], cr=w["CR"], seed=w["seed"],
+                                horizon=w["horizon"], flags=flags)
+        if name == "batched":
+            deoct.deoct_fit_moving_horizon(ctx, ds, prm)  # warm-up: autotuner, graph shapes
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        t0 = time.perf_counter()
+        out = deoct.deoct_fit_moving_horizon(ctx, ds, prm)
+        torch.cuda.synchronize()
+        res[name] = (time.perf_counter() - t0, out, ctx.stats()["launches"])
+    tb, ob, lb = res["batched"]
+    tp, op, lp = res["plain"]
+    same = all(np.array_equal(ob[k], op[k]) for k in ("a", "theta", "kind", "node_fit", "leaf_class"))
+    solves = int(np.sum(ob["kind"] > 0))
+    ranks_np = ds.ranks.cpu().numpy().view(np.uint32)[:, : ds.n]
+    cnt = _mh_node_counts(ranks_np, ob["a"], ob["theta"], w["depth"])
+    de_nodes = np.nonzero(ob["kind"] == 2)[0] + 1
+    evals = int(sum((w["G"] + 1) * w["P"] * int(cnt[t]) for t in de_nodes))
+    ctx.close()
+    return {"workload": MH_WORKLOAD, "subtree_solves": solves,
+            "de_solves": int(len(de_nodes)), "depth1_solves": int(np.sum(ob["kind"] == 1)),
+            "batched_s": tb, "plain_s": tp, "batched_solves_per_s": solves / tb,
+            "plain_solves_per_s": solves / tp, "speedup": tp / tb, "identical_trees": bool(same),
+            "de_evals": evals, "batched_evals_per_s": evals / tb, "plain_evals_per_s": evals / tp,
+            "batched_launches": int(lb), "plain_launches": int(lp)}
+
+
 def run_ours(args):
     import torch
 
@@ -279,6 +335,8 @@ def run_ours(args):
         "clocks": clocks,
         "result": {"fitness": res[2], "train_accuracy": 1.0 - res[2] / n},
     }
+    if world == 1 and not args.no_mh:
+        line["mh_batched_vs_plain"] = mh_compare(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(dict(w, X=data["X"], y=data["y"]))
     print(json.dumps(line), flush=True)
@@ -300,6 +358,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per evaluator launch, when a capture of this kernel exists")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mh", action="store_true", help="skip the batched-vs-plain moving-horizon line")
+    ap.add_argument("--mh-n", type=int, default=1_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
