@@ -242,14 +242,20 @@ def run_serve(args):
     warm = [mk(r, True) for r in raw[: args.slots]]
     for i, w in enumerate(warm):
         w.arrival = 0.0
-    serve.run_trace(srv, warm)
+    try:
+        serve.run_trace(srv, warm)
+    except Exception:
+        srv.close()
+        raise
     srv.peak_in_use = 0
     srv.max_concurrent = 0
     reqs = [mk(r, True) for r in raw]
     t0 = srv.now()
-    res = serve.run_trace(srv, reqs)
-    t1 = srv.now()
-    srv.close()
+    try:
+        res = serve.run_trace(srv, reqs)
+        t1 = srv.now()
+    finally:
+        srv.close()
     lat = serve.latency_stats([r.latency for r in res])
     served = {"requests": len(res), "makespan_s": t1 - t0, "throughput_rps": len(res) / (t1 - t0),
               "latency": lat, "slots": args.slots, "budget_bytes": 120 << 30,
@@ -285,6 +291,44 @@ def run_serve(args):
             "identical_trees_served_vs_alone_plain": bool(same), "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def eval_workload1(args):
+    """Population-evaluation workload at full size: one evaluation of 256 random depth-3
+    trees on n = 1e5 (F = 20, K = 3, uint32 ranks).  Its 8 MB of ranks fit in L2, so L2 is
+    flushed (a 512 MB write) before every timed evaluation."""
+    import torch
+    from paper_2311_06952_gb300 import datagen, deoct
+    w = datagen.make_workload(1)
+    ctx = deoct.Context(torch.cuda.current_device())
+    ds = deoct.encode_dataset(ctx, torch.from_numpy(w["X"]).cuda(), torch.from_numpy(w["y"]).cuda(),
+                              w["K"], w["rank_bytes"])
+    nu = ds.n_unique.cpu().numpy().view(np.uint32)
+    a, th = datagen.random_population(nu, w["P"], w["depth"],
+                                      np.random.Generator(np.random.PCG64(w["pop_seed"])))
+    ad = torch.from_numpy(a.astype(np.int16)).cuda()
+    td = torch.from_numpy(th.view(np.int32)).cuda()
+    L = 1 << w["depth"]
+    counts = torch.empty((w["P"], L, w["K"]), dtype=torch.int32, device="cuda")
+    errs = torch.empty(w["P"], dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    for it in range(args.warmup + args.steps * 4):
+        flush.fill_(it & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        deoct.deoct_eval_population(ctx, ds, ad, td, w["depth"], counts_out=counts, errors_out=errs)
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    ctx.close()
+    ms = float(np.median(times))
+    evals = w["P"] * w["X"].shape[0]
+    return {"workload": "eval-gmm: n=1e5, F=20 Gaussian mixture, K=3, 256 random depth-3 trees, "
+                        "uint32 ranks, one evaluation (pack + evaluate + errors), L2 flushed",
+            "ms": ms, "evals": evals, "evals_per_s": evals / (ms / 1000.0), "samples": len(times)}
 
 
 def run_ours(args):
@@ -398,6 +442,7 @@ def run_ours(args):
         "result": {"fitness": res[2], "train_accuracy": 1.0 - res[2] / n},
     }
     if world == 1 and not args.no_mh:
+        line["population_eval"] = eval_workload1(args)
         line["mh_batched_vs_plain"] = mh_compare(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(dict(w, X=data["X"], y=data["y"]))

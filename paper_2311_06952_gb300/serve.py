@@ -218,8 +218,7 @@ def run_trace(server: Server, requests, time_scale: float = 1.0):
         if delay > 0:
             time.sleep(delay)
         futs.append(server.submit(req))
-    results = [f.result() for f in futs]
-    return results
+    return [f.result() for f in futs]
 
 
 def latency_stats(latencies):
