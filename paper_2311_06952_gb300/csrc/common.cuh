@@ -112,6 +112,22 @@ inline void count_launch(deoct_ctx* ctx, int n = 1) { ctx->launches += (uint64_t
 int check_launch(const char* what);
 int validate_dataset(const deoct_dataset* ds);
 
+// Set a kernel's dynamic shared-memory limit to the largest value the device
+// allows for it (opt-in maximum minus the kernel's static shared memory).  The
+// attribute is per kernel and shared by every host thread, so it is always set
+// to this same value and never to one launch's size.
+template <typename Kern>
+inline int set_max_dynamic_smem(deoct_ctx* ctx, Kern kern) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ctx->max_smem_optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess)
+    return set_error(DEOCT_ERR_CUDA, "setting the shared-memory limit failed: %s", cudaGetErrorString(e));
+  return DEOCT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------

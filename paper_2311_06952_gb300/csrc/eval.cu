@@ -468,11 +468,7 @@ template <int W, int D, int MODE, int Q>
 int launch_t(deoct_ctx* ctx, const EvalArgs& args, const EvalConfig& cfg, size_t smem,
              cudaStream_t s) {
   auto kern = eval_kernel<W, D, MODE, Q>;
-  // The limit is a per-kernel attribute shared by every host thread: always set
-  // it to the device maximum (the same value from every caller), never to this
-  // launch's size, so concurrent callers cannot lower it under each other.
-  DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ctx->max_smem_optin));
+  DEOCT_TRY(set_max_dynamic_smem(ctx, kern));
   // all of the unified L1/shared array as shared memory, so that the occupancy
   // computed below is the residency the launch gets
   DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

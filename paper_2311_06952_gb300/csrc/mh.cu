@@ -410,9 +410,7 @@ int depth1_segments(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     int NT = 256;
     while (NT > 32 && (size_t)NT * K * 4 > 96 * 1024) NT -= 32;
     const size_t sm = (size_t)NT * K * 4;
-    // per-kernel attribute shared by all host threads: the device maximum, always
-    DEOCT_CUDA_TRY(cudaFuncSetAttribute(d1_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        ctx->max_smem_optin));
+    DEOCT_TRY(set_max_dynamic_smem(ctx, d1_sweep_kernel));
     d1_sweep_kernel<<<dim3(Mb, F), NT, sm, s>>>(ks, vs, npad, rs, cn, tot + (size_t)b0 * K, K,
                                                 ds->n_unique, n_min, alpha, F, bf, bth);
     count_launch(ctx);
