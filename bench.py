@@ -40,6 +40,23 @@ WORKLOAD = dict(workload="large-deoct: n=1e7, F=10 U(0,1) quantised to 60000 lev
                 n=10_000_000, F=10, K=2, depth=4, pop=1024, gens=50,
                 l2="inputs larger than L2 (X 400 MB, ranks 200 MB); no flush")
 INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
+# DRAM bytes (read + write) of one evaluator launch on this workload, from the ncu
+# capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
+# kernel source it was taken on (hash of csrc/eval.cu + csrc/common.cuh).
+EVAL_TRAFFIC = {"source_sha256_16": "fa5fec7e9f7a4331", "bytes": 379_089_664 + 3_824_896}
+
+
+def _eval_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("eval.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2311_06952_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_default():
+    return EVAL_TRAFFIC["bytes"] if _eval_source_hash() == EVAL_TRAFFIC["source_sha256_16"] else None
 
 
 def _peaks():
@@ -428,7 +445,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
         "config": w, "gpu_launches": int(st["launches"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": args.traffic,
+                     "frac": achieved / peak,
+                     "traffic": args.traffic if args.traffic is not None else (
+                         _traffic_default() if args.n == WORKLOAD["n"] else None),
                      "kernel": "eval_kernel<2,4,0> (population evaluator)",
                      "ops_per_launch": ops_per_launch, "launch_ms": eval_ms,
                      "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz (%s max clock)" % (
