@@ -143,6 +143,13 @@ DEOCT_API int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32
 DEOCT_API int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
                  void* ranks_out, int64_t ld, uint32_t* n_unique_out, void* stream);
 
+/* As deoct_encode, and also writes the sorted distinct values of every feature
+ * (the xhat_{1..n_p} of Section 3.1) to unique_out [F][ld] float32 (device;
+ * entries n_p..ld-1 of a row are left untouched); unique_out may be NULL. */
+DEOCT_API int deoct_encode_ex(deoct_ctx* ctx, const float* X, int64_t n, int32_t F,
+                              int32_t rank_bytes, void* ranks_out, int64_t ld,
+                              uint32_t* n_unique_out, float* unique_out, void* stream);
+
 /* ---- a2: decoding (Eq. aenc, Eq. benc) ------------------------------------
  * genes [P][2B] float32, individual s_r = [ahat_1..ahat_B, bhat_1..bhat_B],
  * B = 2^depth - 1.  a_t = floor(ahat_t) clamped to {0..F} (0 = no split);
@@ -235,6 +242,26 @@ DEOCT_API int deoct_fit_moving_horizon(deoct_ctx* ctx, const deoct_dataset* ds, 
 DEOCT_API int deoct_depth1_search(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
                         int64_t n_sub, int32_t n_min, double alpha, uint16_t* a_out,
                         uint32_t* theta_out, double* fitness_out, void* stream);
+
+/* ---- prediction with a fitted tree (raw feature values) --------------------
+ * deoct_split_values: the raw-unit threshold of every node, from the sorted
+ * distinct training values `unique` [F][ld] of deoct_encode_ex: for a_t >= 1
+ * and theta_t >= 1, b_t = (xhat_{theta_t} + xhat_{theta_t + 1}) / 2 of feature
+ * a_t (1-based xhat; the midpoints of the threshold set B_p, Section 3.1) in
+ * double; theta_t = 0 gives the smallest training value (beta_{p,1} = 0 after
+ * min-max scaling).  On training samples "x < b_t" routes exactly like
+ * "rank < theta_t".  a, theta [B] in, b_out [B] double out (device). async.
+ * deoct_predict: routes m samples X [m][F] float32 (device) through the tree
+ * (x_{a_t} < b_t -> left, a_t = 0 -> right; Section 2) and writes the leaf
+ * class (leaf_class [2^depth]) to pred_out [m] (nullable); with labels y [m]
+ * it adds the number of correct predictions to *correct_out (device uint64,
+ * zeroed first).  async. */
+DEOCT_API int deoct_split_values(deoct_ctx* ctx, const float* unique, int64_t ld, const uint16_t* a,
+                                 const uint32_t* theta, int32_t B, double* b_out, void* stream);
+DEOCT_API int deoct_predict(deoct_ctx* ctx, const float* X, int64_t m, int32_t F, const uint16_t* a,
+                            const double* b, int32_t depth, const uint8_t* leaf_class,
+                            const uint8_t* y, uint8_t* pred_out, uint64_t* correct_out,
+                            void* stream);
 
 /* ---- evaluation without device allocation --------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot

@@ -252,3 +252,30 @@ def mh(ranks, n_unique, y, K, depth, horizon, P, G, M=0.5, CR=0.9, alpha=0.0, n_
     if rc != ORC_OK:
         raise ValueError("oracle mh failed: %d" % rc)
     return dict(a=a, theta=th, leaf_class=lc, kind=kind, node_fit=nf)
+
+
+def split_values(X, a, theta):
+    """Raw-unit thresholds of a fitted tree (threshold set B_p of Section 3.1): b [B] float64."""
+    X = _c(X, np.float32)
+    a = _c(a, np.int32)
+    theta = _c(theta, np.uint32)
+    n, F = X.shape
+    b = np.empty(len(a), np.float64)
+    rc = lib().orc_split_values(_p(X), ctypes.c_int64(n), ctypes.c_int32(F), _p(a), _p(theta),
+                                ctypes.c_int32(len(a)), _p(b))
+    if rc != ORC_OK:
+        raise ValueError("oracle split_values failed: %d" % rc)
+    return b
+
+
+def predict(X, a, b, depth, leaf_class):
+    """Leaf class of every row of X routed on raw values (Section 2)."""
+    X = _c(X, np.float32)
+    a = _c(a, np.int32)
+    b = _c(b, np.float64)
+    lc = _c(leaf_class, np.uint8)
+    m, F = X.shape
+    out = np.empty(m, np.uint8)
+    lib().orc_predict(_p(X), ctypes.c_int64(m), ctypes.c_int32(F), _p(a), _p(b), ctypes.c_int32(depth),
+                      _p(lc), _p(out))
+    return out

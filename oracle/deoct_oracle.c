@@ -574,3 +574,52 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
   free(seen);
   return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Prediction with a fitted tree on raw values (Section 2 routing with the     */
+/* threshold set B_p of Section 3.1 in raw units).                             */
+/* ------------------------------------------------------------------------- */
+
+/* b_t for node t: with u = the sorted distinct values of feature a_t - 1,
+ * theta_t >= 1 -> (u[theta_t - 1] + u[theta_t]) / 2 (a midpoint of B_p),
+ * theta_t = 0 -> u[0] (beta_1 = 0 after min-max scaling); a_t = 0 -> 0. */
+int orc_split_values(const float* X, int64_t n, int32_t F, const int32_t* a, const uint32_t* theta,
+                     int32_t B, double* b_out) {
+  float* col = (float*)malloc((size_t)n * sizeof(float));
+  if (!col) return ORC_ERR_OOM;
+  for (int32_t t = 0; t < B; ++t) {
+    if (a[t] == 0) { b_out[t] = 0.0; continue; }
+    int32_t p = a[t] - 1;
+    if (p >= F) { free(col); return ORC_ERR_INVALID; }
+    for (int64_t i = 0; i < n; ++i) {
+      float v = X[i * F + p];
+      if (v == 0.0f) v = 0.0f;
+      col[i] = v;
+    }
+    qsort(col, (size_t)n, sizeof(float), cmp_float);
+    int64_t np = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (np == 0 || col[i] != col[np - 1]) col[np++] = col[i];
+    if ((int64_t)theta[t] >= np) { free(col); return ORC_ERR_INVALID; }
+    b_out[t] = theta[t] == 0 ? (double)col[0]
+                             : ((double)col[theta[t] - 1] + (double)col[theta[t]]) * 0.5;
+  }
+  free(col);
+  return ORC_OK;
+}
+
+/* Route every row of X [m][F] (x_{a_t} < b_t -> left, a_t = 0 -> right) and
+ * output its leaf's class. */
+void orc_predict(const float* X, int64_t m, int32_t F, const int32_t* a, const double* b,
+                 int32_t depth, const uint8_t* leaf_class, uint8_t* pred) {
+  int32_t B = (1 << depth) - 1;
+  for (int64_t i = 0; i < m; ++i) {
+    int32_t t = 1;
+    while (t <= B) {
+      int32_t at = a[t - 1];
+      int left = (at != 0) && ((double)X[i * F + (at - 1)] < b[t - 1]);
+      t = left ? 2 * t : 2 * t + 1;
+    }
+    pred[i] = leaf_class[t - (B + 1)];
+  }
+}

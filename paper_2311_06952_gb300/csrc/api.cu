@@ -353,6 +353,12 @@ int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, 
 
 int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
                  void* ranks_out, int64_t ld, uint32_t* n_unique_out, void* stream) {
+  return deoct_encode_ex(ctx, X, n, F, rank_bytes, ranks_out, ld, n_unique_out, nullptr, stream);
+}
+
+int deoct_encode_ex(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
+                    void* ranks_out, int64_t ld, uint32_t* n_unique_out, float* unique_out,
+                    void* stream) {
   API_BEGIN
   CTX_CHECK(ctx);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -361,7 +367,7 @@ int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t r
   if (F < 1 || F > kMaxF) return set_error(DEOCT_ERR_INVALID, "F = %d outside 1..256", F);
   if (rank_bytes != 2 && rank_bytes != 4) return set_error(DEOCT_ERR_INVALID, "rank_bytes must be 2 or 4");
   if (ld < n) return set_error(DEOCT_ERR_INVALID, "ld < n");
-  DEOCT_TRY(encode_run(ctx, X, n, F, rank_bytes, ranks_out, ld, n_unique_out, s));
+  DEOCT_TRY(encode_run(ctx, X, n, F, rank_bytes, ranks_out, ld, n_unique_out, unique_out, s));
   DEOCT_TRY(check_status(ctx, s));
   if (rank_bytes == 2) {
     uint32_t* h = nullptr;
@@ -374,6 +380,32 @@ int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t r
                          f, h[f]);
   }
   return DEOCT_OK;
+  API_END
+}
+
+int deoct_split_values(deoct_ctx* ctx, const float* unique, int64_t ld, const uint16_t* a,
+                       const uint32_t* theta, int32_t B, double* b_out, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  if (!unique || !a || !theta || !b_out) return set_error(DEOCT_ERR_INVALID, "NULL pointer");
+  if (B < 1 || B > (1 << kMaxDepth) - 1) return set_error(DEOCT_ERR_INVALID, "B = %d out of range", B);
+  if (ld < 1) return set_error(DEOCT_ERR_INVALID, "ld < 1");
+  return launch_split_values(ctx, unique, ld, a, theta, B, b_out, static_cast<cudaStream_t>(stream));
+  API_END
+}
+
+int deoct_predict(deoct_ctx* ctx, const float* X, int64_t m, int32_t F, const uint16_t* a,
+                  const double* b, int32_t depth, const uint8_t* leaf_class, const uint8_t* y,
+                  uint8_t* pred_out, uint64_t* correct_out, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  if (!X || !a || !b || !leaf_class) return set_error(DEOCT_ERR_INVALID, "NULL pointer");
+  if (m < 0 || F < 1 || F > kMaxF) return set_error(DEOCT_ERR_INVALID, "bad m or F");
+  if (depth < 1 || depth > kMaxDepth) return set_error(DEOCT_ERR_INVALID, "depth out of range");
+  if (correct_out && !y) return set_error(DEOCT_ERR_INVALID, "correct_out needs labels y");
+  return launch_predict(ctx, X, m, F, a, b, depth, leaf_class, y, pred_out,
+                        reinterpret_cast<unsigned long long*>(correct_out),
+                        static_cast<cudaStream_t>(stream));
   API_END
 }
 

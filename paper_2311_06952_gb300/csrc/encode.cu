@@ -22,6 +22,9 @@ __device__ __forceinline__ uint32_t orderable(float v) {
   uint32_t b = __float_as_uint(v);
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
+__device__ __forceinline__ float from_orderable(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
 
 // block-wide exclusive scan of one value per thread (blockDim.x == kThreads)
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot,
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) rank_scan_kernel(uint32_t* __restric
 template <typename RT>
 __global__ void __launch_bounds__(kThreads) rank_scatter_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int ntiles,
-    const uint32_t* __restrict__ C, RT* __restrict__ ranks, int64_t ld) {
+    const uint32_t* __restrict__ C, RT* __restrict__ ranks, int64_t ld, float* __restrict__ uniq) {
   __shared__ uint32_t wt[kThreads / 32];
   const int f = blockIdx.y, tile = blockIdx.x;
   const uint32_t* k = keys + (int64_t)f * n;
@@ -233,7 +236,10 @@ __global__ void __launch_bounds__(kThreads) rank_scatter_kernel(
   for (int e = 0; e < kItems; ++e) {
     int64_t j = j0 + e;
     r += flags[e];
-    if (j < n) out[v[j]] = (RT)(r - 1u);
+    if (j < n) {
+      out[v[j]] = (RT)(r - 1u);
+      if (uniq && flags[e]) uniq[(int64_t)f * ld + (r - 1u)] = from_orderable(k[j]);
+    }
   }
 }
 
@@ -264,7 +270,7 @@ int radix_sort_segments(deoct_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1
 }
 
 int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ranks_out,
-               int64_t ld, uint32_t* n_unique_out, cudaStream_t s) {
+               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s) {
   const size_t elems = (size_t)n * F;
   uint32_t *k0, *k1, *v0, *v1, *C;
   DEOCT_TRY(scratch_get(ctx, SL_ENC_K0, elems * 4, (void**)&k0));
@@ -286,10 +292,12 @@ int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ra
   rank_scan_kernel<<<F, kThreads, 0, s>>>(C, ntiles, n_unique_out);
   if (W == 2)
     rank_scatter_kernel<uint16_t><<<g, kThreads, 0, s>>>(ks, vs, n, ntiles, C,
-                                                        static_cast<uint16_t*>(ranks_out), ld);
+                                                        static_cast<uint16_t*>(ranks_out), ld,
+                                                        unique_out);
   else
     rank_scatter_kernel<uint32_t><<<g, kThreads, 0, s>>>(ks, vs, n, ntiles, C,
-                                                        static_cast<uint32_t*>(ranks_out), ld);
+                                                        static_cast<uint32_t*>(ranks_out), ld,
+                                                        unique_out);
   count_launch(ctx, 3);
   return check_launch("rank kernels");
 }

@@ -114,7 +114,16 @@ int launch_decode(deoct_ctx* ctx, const float* genes, int P, int depth, int F,
 // encoder (encode.cu)
 // ---------------------------------------------------------------------------
 int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ranks_out,
-               int64_t ld, uint32_t* n_unique_out, cudaStream_t s);
+               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// prediction (predict.cu)
+// ---------------------------------------------------------------------------
+int launch_split_values(deoct_ctx* ctx, const float* unique, int64_t ld, const uint16_t* a,
+                        const uint32_t* theta, int B, double* b_out, cudaStream_t s);
+int launch_predict(deoct_ctx* ctx, const float* X, int64_t m, int F, const uint16_t* a,
+                   const double* b, int depth, const uint8_t* leaf_class, const uint8_t* y,
+                   uint8_t* pred_out, unsigned long long* correct_out, cudaStream_t s);
 
 // segmented LSD radix sort of uint32 keys with uint32 values; F segments of
 // length n each, stored back to back.  Sorts `bits` low key bits.  On return

@@ -31,7 +31,7 @@ EXPORTED = [
     "deoct_set_timing", "deoct_get_stats", "deoct_reset_stats", "deoct_encode",
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
     "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
-    "deoct_eval_population_noalloc",
+    "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -88,6 +88,9 @@ def load(path: str | None = None):
             "deoct_reset_stats": [_vp],
             "deoct_set_eval_config": [_vp, _i32, _i32, _i32, _i32],
             "deoct_encode": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp],
+            "deoct_encode_ex": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
+            "deoct_split_values": [_vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp],
+            "deoct_predict": [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
             "deoct_decode_population": [_vp, ctypes.POINTER(Dataset), _vp, _i32, _i32, _vp, _vp, _vp],
             "deoct_eval_population": [_vp, ctypes.POINTER(Dataset), _vp, _i64, _vp, _vp, _i32, _i32,
                                       _vp, _vp, _vp],
@@ -205,6 +208,41 @@ def deoct_encode(ctx: Context, X, rank_bytes: int, ranks_out=None, n_unique_out=
     _check(load().deoct_encode(ctx.handle, _ptr(X), n, F, rank_bytes, _ptr(ranks_out),
                                ranks_out.shape[1], _ptr(n_unique_out), _stream(stream)))
     return ranks_out, n_unique_out
+
+
+def deoct_encode_ex(ctx: Context, X, rank_bytes: int, stream=None):
+    """a1 plus the sorted distinct values: (ranks [F][ld], n_unique [F], unique [F][ld] float32)."""
+    import torch
+    n, F = X.shape
+    dt = torch.int16 if rank_bytes == 2 else torch.int32
+    ld = padded_ld(n, rank_bytes)
+    ranks = torch.empty((F, ld), dtype=dt, device=X.device)
+    nu = torch.empty(F, dtype=torch.int32, device=X.device)
+    uniq = torch.empty((F, ld), dtype=torch.float32, device=X.device)
+    _check(load().deoct_encode_ex(ctx.handle, _ptr(X), n, F, rank_bytes, _ptr(ranks), ld, _ptr(nu),
+                                  _ptr(uniq), _stream(stream)))
+    return ranks, nu, uniq
+
+
+def deoct_split_values(ctx: Context, unique, a, theta, stream=None):
+    """Raw-unit thresholds b [B] (float64, device) of a fitted tree (a, theta: device [B])."""
+    import torch
+    B = a.numel()
+    b = torch.empty(B, dtype=torch.float64, device=unique.device)
+    _check(load().deoct_split_values(ctx.handle, _ptr(unique), unique.shape[1], _ptr(a), _ptr(theta), B,
+                                     _ptr(b), _stream(stream)))
+    return b
+
+
+def deoct_predict(ctx: Context, X, a, b, depth: int, leaf_class, y=None, stream=None):
+    """Leaf class of every row of X [m][F] (device); with labels, also the count of correct ones."""
+    import torch
+    m, F = X.shape
+    pred = torch.empty(m, dtype=torch.uint8, device=X.device)
+    correct = torch.zeros(1, dtype=torch.int64, device=X.device) if y is not None else None
+    _check(load().deoct_predict(ctx.handle, _ptr(X), m, F, _ptr(a), _ptr(b), depth, _ptr(leaf_class),
+                                _ptr(y), _ptr(pred), _ptr(correct), _stream(stream)))
+    return pred, correct
 
 
 def encode_dataset(ctx: Context, X, y, K: int, rank_bytes: int, stream=None) -> DeviceDataset:

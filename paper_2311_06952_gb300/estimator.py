@@ -1,0 +1,94 @@
+"""A fit / predict interface over the C ABI (MH-DEOCT and DEOCT classifiers).
+
+Marshalling and orchestration only: encoding, the moving-horizon fit, the raw
+thresholds and the prediction all run in libdeoct's kernels.
+
+Presets follow Section 5 of the paper: "normal" is population 100, 600
+generations, CR 0.1, M = rand(0,1) per individual (dithered); "long" is
+population 200 and 4000 generations.  The moving-horizon depth defaults to 2
+for depth-2 trees and 3 otherwise (Section 5.2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PRESETS = {
+    "normal": dict(pop=100, gens=600, cr=0.1, mut_f=0.5, dither=True),
+    "long": dict(pop=200, gens=4000, cr=0.1, mut_f=0.5, dither=True),
+}
+
+
+class MHDEOCTClassifier:
+    """Moving-horizon DEOCT (Algorithm 2).  ``horizon >= depth`` is plain DEOCT
+    of the whole tree at the root, kept node by node."""
+
+    def __init__(self, depth=3, horizon=None, preset="normal", pop=None, gens=None, cr=None, mut_f=None,
+                 dither=None, alpha=0.0, n_min=1, seed=0, batched=True, device=0):
+        p = dict(PRESETS[preset])
+        for k, v in dict(pop=pop, gens=gens, cr=cr, mut_f=mut_f, dither=dither).items():
+            if v is not None:
+                p[k] = v
+        self.depth = int(depth)
+        self.horizon = int(horizon) if horizon is not None else (2 if depth == 2 else 3)
+        self.params = p
+        self.alpha, self.n_min, self.seed = float(alpha), int(n_min), int(seed)
+        self.batched = bool(batched)
+        self.device = device
+        self.tree_ = None
+        self._ctx = None
+
+    def _context(self):
+        from . import deoct
+        if self._ctx is None:
+            self._ctx = deoct.Context(self.device)
+        return self._ctx
+
+    @staticmethod
+    def _dev(a, dtype):
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.to(device="cuda", dtype=dtype).contiguous()
+        return torch.from_numpy(np.ascontiguousarray(a)).to("cuda").to(dtype).contiguous()
+
+    def fit(self, X, y, K=None):
+        import torch
+
+        from . import deoct
+        ctx = self._context()
+        Xd = self._dev(X, torch.float32)
+        yd = self._dev(y, torch.uint8)
+        n, F = Xd.shape
+        K = int(K) if K is not None else int(yd.max().item()) + 1
+        rank_bytes = 2 if n <= 65536 else 4
+        ranks, nu, uniq = deoct.deoct_encode_ex(ctx, Xd, rank_bytes)
+        ds = deoct.DeviceDataset(ranks, rank_bytes, nu, yd, n, F, K)
+        flags = (deoct.DEOCT_BATCHED if self.batched else 0) | \
+            (deoct.DEOCT_DITHER_M if self.params["dither"] else 0)
+        prm = deoct.make_params(self.depth, self.params["pop"], self.params["gens"],
+                                mut_f=self.params["mut_f"], cr=self.params["cr"], alpha=self.alpha,
+                                n_min=self.n_min, seed=self.seed, horizon=self.horizon, flags=flags)
+        out = deoct.deoct_fit_moving_horizon(ctx, ds, prm)
+        a = torch.from_numpy(out["a"].view(np.int16)).cuda()
+        th = torch.from_numpy(out["theta"].view(np.int32)).cuda()
+        b = deoct.deoct_split_values(ctx, uniq, a, th)
+        self.tree_ = dict(out, b=b.cpu().numpy(), K=K, F=F)
+        self._dev_tree = (a, b, torch.from_numpy(out["leaf_class"]).cuda())
+        return self
+
+    def predict(self, X):
+        import torch
+
+        from . import deoct
+        a, b, lc = self._dev_tree
+        pred, _ = deoct.deoct_predict(self._context(), self._dev(X, torch.float32), a, b, self.depth, lc)
+        return pred.cpu().numpy()
+
+    def score(self, X, y):
+        import torch
+
+        from . import deoct
+        a, b, lc = self._dev_tree
+        Xd = self._dev(X, torch.float32)
+        _, correct = deoct.deoct_predict(self._context(), Xd, a, b, self.depth, lc,
+                                         y=self._dev(y, torch.uint8))
+        return int(correct.item()) / Xd.shape[0]

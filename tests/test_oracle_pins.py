@@ -483,3 +483,40 @@ def test_mh_root_is_deoct_root_when_horizon_covers_depth():
     assert out["kind"][0] == 2
     assert out["a"][0] == a[0, 0] and out["theta"][0] == th[0, 0]
     assert out["node_fit"][0] == de["fit"][de["best"]]
+
+
+# --------------------------------------------------------------------------
+# Raw-unit thresholds and prediction (Section 3.1 threshold set, Section 2 routing)
+# --------------------------------------------------------------------------
+
+def test_split_values_route_training_samples_like_ranks():
+    rng = _rng(61)
+    n, F, K, depth = 3000, 5, 3, 3
+    X = np.round(rng.normal(size=(n, F)), 2).astype(np.float32)
+    X[:, 4] = -1.5
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    for trial in range(10):
+        a, th = datagen.random_population(nu, 1, depth, rng, allow_nosplit=True)
+        counts = oracle.eval_counts(ranks, y, K, a, th, depth)
+        lc = oracle.leaf_classes(counts)[0]
+        b = oracle.split_values(X, a[0], th[0])
+        pred = oracle.predict(X, a[0], b, depth, lc)
+        # the same samples, routed on ranks in numpy
+        t = np.ones(n, np.int64)
+        B = (1 << depth) - 1
+        for _ in range(depth):
+            at = a[0][t - 1]
+            rk = ranks[np.maximum(at - 1, 0), np.arange(n)]
+            t = np.where((at > 0) & (rk < th[0][t - 1]), 2 * t, 2 * t + 1)
+        np.testing.assert_array_equal(pred, lc[t - (B + 1)])
+        # loss identity: misclassified training samples = fitness errors
+        _, err, _, _ = oracle.fitness(counts, a, n)
+        assert int(np.sum(pred != y)) == int(err[0])
+
+
+def test_split_values_definition():
+    X = np.array([[3.0], [1.0], [2.0], [2.0], [7.0]], np.float32)
+    b = oracle.split_values(X, np.array([1, 1, 1, 0]), np.array([0, 1, 3, 0], np.uint32))
+    # sorted distinct values 1, 2, 3, 7
+    assert list(b) == [1.0, 1.5, 5.0, 0.0]
