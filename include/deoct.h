@@ -51,6 +51,7 @@ typedef enum {
 /* deoct_params.flags */
 #define DEOCT_DITHER_M 0x1u /* M = rand(0,1) per (generation, individual), Section 3.3 */
 #define DEOCT_BATCHED 0x2u  /* moving horizon: one batched launch per level */
+#define DEOCT_CART_SEEDS 0x4u /* moving horizon: seed each DEOCT subtree with its greedy tree */
 
 typedef struct deoct_ctx deoct_ctx;
 
@@ -227,6 +228,11 @@ DEOCT_API int deoct_fit_subtree(deoct_ctx* ctx, const deoct_dataset* ds, const i
  * DEOCT_BATCHED in params->flags solves all nodes of a level in one batched
  * launch per generation over a compacted sample index; otherwise each node is
  * a separate DEOCT (the plain per-node form).  Both give identical trees.
+ * DEOCT_CART_SEEDS adds the CART warm start of Algorithm 2: slot 0 of each
+ * DEOCT subtree's initial population is the greedy misclassification tree of
+ * depth D_t on X_t (the depth-1 search applied top-down inside the subtree,
+ * same solve rule and tie order), encoded as genes a + 1/2 and the float32
+ * bhat nearest to (theta + 1/2)/(n_p + 1) that decodes to theta.
  *  a_out [2^D - 1] uint16, theta_out [2^D - 1] uint32, leaf_class_out [2^D]
  *  uint8 (Eq. opt_c on the whole set, lowest class on ties): host arrays.
  *  kind_out [2^D - 1] int32 (0 artificial, 1 depth-1 search, 2 DEOCT) and

@@ -63,7 +63,7 @@ class MHParams(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("horizon", ctypes.c_int32), ("P", ctypes.c_int32),
                 ("G", ctypes.c_int32), ("M", ctypes.c_float), ("CR", ctypes.c_float),
                 ("alpha", ctypes.c_double), ("n_min", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("dither", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("dither", ctypes.c_int32), ("cart_seeds", ctypes.c_int32)]
 
 
 def lib():
@@ -233,15 +233,34 @@ def depth1(ranks, n_unique, y, K, idx=None, n_min=1, alpha=0.0):
     return a.value, th.value, f.value
 
 
+def greedy_tree(ranks, n_unique, y, K, depth, idx=None, n_min=1, alpha=0.0):
+    """Greedy misclassification tree (the CART warm start of Algorithm 2): (a [B], theta [B])."""
+    ranks = _c(ranks, np.uint32)
+    nu = _c(n_unique, np.uint32)
+    y = _c(y, np.uint8)
+    F, n = ranks.shape
+    B = (1 << depth) - 1
+    idx_arr = None if idx is None else _c(idx, np.int32)
+    n_sub = n if idx is None else len(idx_arr)
+    a = np.empty(B, np.int32)
+    th = np.empty(B, np.uint32)
+    rc = lib().orc_greedy_tree(_p(ranks), ctypes.c_int64(n), ctypes.c_int32(F), _p(nu), _p(y),
+                               ctypes.c_int32(K), _p(idx_arr), ctypes.c_int64(n_sub), ctypes.c_int32(depth),
+                               ctypes.c_int32(n_min), ctypes.c_double(alpha), _p(a), _p(th))
+    if rc != ORC_OK:
+        raise ValueError("oracle greedy_tree failed: %d" % rc)
+    return a, th
+
+
 def mh(ranks, n_unique, y, K, depth, horizon, P, G, M=0.5, CR=0.9, alpha=0.0, n_min=1, seed=0,
-       dither=False):
+       dither=False, cart_seeds=False):
     """Algorithm 2 (moving-horizon DEOCT): dict(a, theta, leaf_class, kind, node_fit)."""
     ranks = _c(ranks, np.uint32)
     nu = _c(n_unique, np.uint32)
     y = _c(y, np.uint8)
     F, n = ranks.shape
     B = (1 << depth) - 1
-    prm = MHParams(depth, horizon, P, G, M, CR, alpha, n_min, seed, int(dither))
+    prm = MHParams(depth, horizon, P, G, M, CR, alpha, n_min, seed, int(dither), int(cart_seeds))
     a = np.empty(B, np.int32)
     th = np.empty(B, np.uint32)
     lc = np.empty(1 << depth, np.uint8)

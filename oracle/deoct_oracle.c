@@ -475,7 +475,63 @@ typedef struct {
   int32_t n_min;
   uint64_t seed;
   int32_t dither;
+  int32_t cart_seeds; /* 1: CART warm start in slot 0 of every DEOCT subtree */
 } orc_mh_params;
+
+/* Greedy misclassification tree of depth D on the samples idx[0..n_sub-1]
+ * (Reading: the "CART solution" of Algorithm 2 is the exhaustive depth-1
+ * search applied top-down; a node is split only if it has more than n_min
+ * samples and two classes, as in Algorithm 2).  a_out, theta_out [2^D - 1]. */
+int orc_greedy_tree(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique,
+                    const uint8_t* y, int32_t K, const int32_t* idx, int64_t n_sub, int32_t depth,
+                    int32_t n_min, double alpha, int32_t* a_out, uint32_t* theta_out) {
+  int32_t B = (1 << depth) - 1;
+  int64_t m = idx ? n_sub : n;
+  int32_t* sub = (int32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+  uint8_t* seen = (uint8_t*)malloc((size_t)K);
+  if (!sub || !seen) { free(sub); free(seen); return ORC_ERR_OOM; }
+  for (int32_t t = 0; t < B; ++t) { a_out[t] = 0; theta_out[t] = 0; }
+  int rc = ORC_OK;
+  for (int32_t t = 1; t <= B && rc == ORC_OK; ++t) {
+    int32_t d = 0;
+    while ((1 << (d + 1)) <= t) ++d;
+    int64_t nt = 0;
+    for (int64_t j = 0; j < m; ++j) {
+      int64_t i = idx ? idx[j] : j;
+      int32_t u = 1;
+      for (int32_t l = 0; l < d; ++l) {
+        int32_t au = a_out[u - 1];
+        int left = (au != 0) && (ranks[(int64_t)(au - 1) * n + i] < theta_out[u - 1]);
+        u = left ? 2 * u : 2 * u + 1;
+      }
+      if (u == t) sub[nt++] = (int32_t)i;
+    }
+    memset(seen, 0, (size_t)K);
+    int32_t ncls = 0;
+    for (int64_t j = 0; j < nt; ++j)
+      if (!seen[y[sub[j]]]) { seen[y[sub[j]]] = 1; ++ncls; }
+    if (!(nt > n_min && ncls > 1)) continue;
+    double f;
+    rc = orc_depth1(ranks, n, F, n_unique, y, K, sub, nt, n_min, alpha, &a_out[t - 1],
+                    &theta_out[t - 1], &f);
+  }
+  free(sub);
+  free(seen);
+  return rc;
+}
+
+/* Genes of a decoded node (inverse of Eq. aenc / Eq. benc): ahat = a + 1/2;
+ * bhat = the float32 nearest (theta + 1/2) / (n_p + 1), moved one float at a
+ * time until floor(bhat (n_p + 1)) = theta. */
+static void node_genes(int32_t a, uint32_t theta, uint32_t np, float* ahat, float* bhat) {
+  *ahat = (float)a + 0.5f;
+  if (a == 0) { *bhat = 0.0f; return; }
+  double np1 = (double)np + 1.0;
+  float b = (float)(((double)theta + 0.5) / np1);
+  for (int it = 0; it < 64 && floor((double)b * np1) > (double)theta; ++it) b = nextafterf(b, 0.0f);
+  for (int it = 0; it < 64 && floor((double)b * np1) < (double)theta; ++it) b = nextafterf(b, 1.0f);
+  *bhat = b;
+}
 
 /* Algorithm 2 over the branch nodes t = 1..2^D-1 in BFS order.  For node t at
  * depth d (root d = 0, as in the Fig. 3 example of Section 4):
@@ -531,10 +587,30 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
       int32_t Bt = (1 << Dt) - 1;
       float* pop = (float*)malloc((size_t)prm->P * 2 * Bt * sizeof(float));
       double* fit = (double*)malloc((size_t)prm->P * sizeof(double));
-      if (!pop || !fit) { free(pop); free(fit); rc = ORC_ERR_OOM; break; }
+      float* seed_genes = (float*)malloc((size_t)2 * Bt * sizeof(float));
+      int32_t* ga = (int32_t*)malloc((size_t)Bt * sizeof(int32_t));
+      uint32_t* gth = (uint32_t*)malloc((size_t)Bt * sizeof(uint32_t));
+      if (!pop || !fit || !seed_genes || !ga || !gth) {
+        free(pop); free(fit); free(seed_genes); free(ga); free(gth);
+        rc = ORC_ERR_OOM;
+        break;
+      }
+      int32_t S = 0;
+      if (prm->cart_seeds) {
+        rc = orc_greedy_tree(ranks, n, F, n_unique, y, K, sub, nt, Dt, prm->n_min, prm->alpha, ga,
+                             gth);
+        for (int32_t q = 0; q < Bt && rc == ORC_OK; ++q)
+          node_genes(ga[q], gth[q], ga[q] > 0 ? n_unique[ga[q] - 1] : 1u, &seed_genes[q],
+                     &seed_genes[Bt + q]);
+        S = 1;
+      }
       int32_t best = 0;
-      rc = orc_de_run(ranks, n, F, n_unique, y, K, sub, nt, &dp, NULL, 0, pop, fit, &best,
-                      NULL, NULL, NULL);
+      if (rc == ORC_OK)
+        rc = orc_de_run(ranks, n, F, n_unique, y, K, sub, nt, &dp, S ? seed_genes : NULL, S, pop,
+                        fit, &best, NULL, NULL, NULL);
+      free(seed_genes);
+      free(ga);
+      free(gth);
       if (rc == ORC_OK) {
         int32_t a1;
         uint32_t th1;

@@ -19,6 +19,7 @@
 //     counts; the best split per node is reduced over features.
 // Then the samples move one level down.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -329,10 +330,11 @@ struct Compacted {
 
 // Gather the samples listed in idx (already filled, -1 = padding) into the
 // compacted rank rows and labels.
-int gather_compacted(deoct_ctx* ctx, const deoct_dataset* ds, Compacted* c, cudaStream_t s) {
+int gather_compacted(deoct_ctx* ctx, const deoct_dataset* ds, Compacted* c, cudaStream_t s,
+                     int slot_ranks = SL_MH_RANKS, int slot_labels = SL_MH_LABELS) {
   const int W = ds->rank_bytes;
-  DEOCT_TRY(scratch_get(ctx, SL_MH_RANKS, (size_t)ds->F * c->npad * W, &c->cranks));
-  DEOCT_TRY(scratch_get(ctx, SL_MH_LABELS, (size_t)c->npad, (void**)&c->clabels));
+  DEOCT_TRY(scratch_get(ctx, slot_ranks, (size_t)ds->F * c->npad * W, &c->cranks));
+  DEOCT_TRY(scratch_get(ctx, slot_labels, (size_t)c->npad, (void**)&c->clabels));
   dim3 g((unsigned)((c->npad + 255) / 256), ds->F);
   if (W == 2)
     gather_kernel<uint16_t><<<g, 256, 0, s>>>(static_cast<const uint16_t*>(ds->ranks), ds->ld, ds->labels,
@@ -483,8 +485,8 @@ uint64_t tune_key(int W, int D, int F, int K, int P, int64_t npad, int M) {
 // step launch per generation, replayed from a captured CUDA graph.
 int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
                const std::vector<int>& node_ids, int Dt, const deoct_params* prm,
-               std::vector<uint16_t>* ra, std::vector<uint32_t>* rth, std::vector<double>* rf,
-               cudaStream_t s) {
+               const float* d_seeds, std::vector<uint16_t>* ra, std::vector<uint32_t>* rth,
+               std::vector<double>* rf, cudaStream_t s) {
   const int M = (int)node_ids.size();
   const int P = prm->pop, B = (1 << Dt) - 1, L = 1 << Dt, m2 = 2 * B, K = ds->K, F = ds->F;
   const int W = ds->rank_bytes;
@@ -515,10 +517,10 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     d.nodes = reinterpret_cast<uint32_t*>(take((size_t)P * B * 4));
     d.counts = reinterpret_cast<uint32_t*>(take((size_t)P * L * K * 4));
     d.n_unique = ds->n_unique;
-    d.seeds = nullptr;
+    d.seeds = d_seeds ? d_seeds + (size_t)m * m2 : nullptr;
     d.n_valid = c.counts[m];
     d.stream_id = (uint64_t)node_ids[m];
-    d.S = 0;
+    d.S = d_seeds ? 1 : 0;
     d.F = F;
     d.K = K;
     EvalProb& e = be.probs[m];
@@ -675,7 +677,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
 
 // Plain form: one DEOCT (own launches) per node segment.
 int de_plain(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
-             const std::vector<int>& node_ids, int Dt, const deoct_params* prm,
+             const std::vector<int>& node_ids, int Dt, const deoct_params* prm, const float* d_seeds,
              std::vector<uint16_t>* ra, std::vector<uint32_t>* rth, std::vector<double>* rf,
              cudaStream_t s) {
   const int M = (int)node_ids.size();
@@ -698,7 +700,9 @@ int de_plain(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   rf->resize(M);
   for (int m = 0; m < M; ++m) {
     deoct_dataset v = segment_view(ds, c, m);
-    DEOCT_TRY(run_deoct(ctx, &v, nullptr, v.n, &dp, (uint64_t)node_ids[m], nullptr, 0, pop, fit, best, s));
+    const float* sd = d_seeds ? d_seeds + (size_t)m * 2 * B : nullptr;
+    DEOCT_TRY(run_deoct(ctx, &v, nullptr, v.n, &dp, (uint64_t)node_ids[m], sd, sd ? 1 : 0, pop, fit,
+                        best, s));
     DEOCT_TRY(launch_best_extract(ctx, pop, fit, best, Dt, ds->F, ds->n_unique, da, dth, df, s));
     std::vector<double> hf;
     std::vector<uint32_t> hth;
@@ -710,6 +714,191 @@ int de_plain(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     (*rth)[m] = hth[0];
     (*rf)[m] = hf[0];
   }
+  return DEOCT_OK;
+}
+
+// ---- CART warm starts: greedy misclassification subtrees of every segment ----
+
+// class histogram of (segment, subtree node) at one subtree depth
+__global__ void sub_hist_kernel(const int32_t* __restrict__ pos_slot, const int32_t* __restrict__ sub_of,
+                                const uint8_t* __restrict__ clabels, int64_t npad, int32_t base,
+                                int32_t nsub, int K, uint32_t* __restrict__ hist) {
+  int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= npad) return;
+  const int m = pos_slot[pos];
+  if (m < 0) return;
+  const int k = sub_of[pos] - base;
+  const int y = clabels[pos];
+  if (k < 0 || k >= nsub || y >= K) return;
+  atomicAdd(&hist[((int64_t)m * nsub + k) * K + y], 1u);
+}
+
+// positions of solved (segment, subtree node) pairs -> a new compacted set
+__global__ void sub_compact_kernel(const int32_t* __restrict__ pos_slot, const int32_t* __restrict__ sub_of,
+                                   const int32_t* __restrict__ idx, int64_t npad, int32_t base, int32_t nsub,
+                                   const int32_t* __restrict__ slot2_of, const int64_t* __restrict__ seg_off2,
+                                   int32_t* __restrict__ cursor2, int32_t* __restrict__ idx2,
+                                   int32_t* __restrict__ pos_slot2) {
+  int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int m2 = -1;
+  if (pos < npad) {
+    const int m = pos_slot[pos];
+    if (m >= 0) {
+      const int k = sub_of[pos] - base;
+      if (k >= 0 && k < nsub) m2 = slot2_of[(int64_t)m * nsub + k];
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, m2);
+  const int leader = __ffs(peers) - 1;
+  int basepos = 0;
+  if (m2 >= 0 && lane == leader) basepos = atomicAdd(&cursor2[m2], __popc(peers));
+  basepos = __shfl_sync(0xFFFFFFFFu, basepos, leader);
+  if (m2 >= 0) {
+    const int64_t p2 = seg_off2[m2] + basepos + __popc(peers & ((1u << lane) - 1u));
+    idx2[p2] = idx[pos];
+    pos_slot2[p2] = m2;
+  }
+}
+
+// one subtree level down inside every segment
+template <typename RT>
+__global__ void sub_route_kernel(const int32_t* __restrict__ pos_slot, int32_t* __restrict__ sub_of,
+                                 const int32_t* __restrict__ idx, const RT* __restrict__ ranks, int64_t ld,
+                                 int64_t npad, int32_t base, int32_t nsub,
+                                 const uint32_t* __restrict__ packed) {
+  int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= npad) return;
+  const int m = pos_slot[pos];
+  if (m < 0) return;
+  const int t = sub_of[pos];
+  const int k = t - base;
+  if (k < 0 || k >= nsub) return;
+  const uint32_t pk = packed[(int64_t)m * nsub + k];
+  const uint32_t f = pk >> 24, th = pk & kThetaMask;
+  const uint32_t r = ranks[(int64_t)f * ld + idx[pos]];
+  sub_of[pos] = 2 * t + (r < th ? 0 : 1);
+}
+
+// genes of one decoded node: ahat = a + 1/2; bhat = the float32 nearest to
+// (theta + 1/2) / (n_p + 1), nudged until floor(bhat (n_p + 1)) = theta
+void encode_node_genes(int a, uint32_t theta, uint32_t np, float* ahat, float* bhat) {
+  *ahat = (float)a + 0.5f;
+  if (a == 0) {
+    *bhat = 0.0f;
+    return;
+  }
+  const double np1 = (double)np + 1.0;
+  float b = (float)(((double)theta + 0.5) / np1);
+  for (int it = 0; it < 64 && std::floor((double)b * np1) > (double)theta; ++it) b = std::nextafter(b, 0.0f);
+  for (int it = 0; it < 64 && std::floor((double)b * np1) < (double)theta; ++it) b = std::nextafter(b, 1.0f);
+  *bhat = b;
+}
+
+// Greedy depth-Dt subtree of every segment of c (CART warm starts of
+// Algorithm 2): per subtree depth r, solved (segment, node) pairs get the
+// exhaustive depth-1 split of their samples.  Result: genes [M][2B] (device).
+int greedy_seeds(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c, int Dt,
+                 const deoct_params* prm, float** d_seeds, cudaStream_t s) {
+  const int M = (int)c.counts.size();
+  const int B = (1 << Dt) - 1, K = ds->K;
+  int32_t* sub_of;
+  DEOCT_TRY(scratch_get(ctx, SL_MH_SUB, sizeof(int32_t) * c.npad, (void**)&sub_of));
+  DEOCT_TRY(launch_fill(ctx, sub_of, c.npad, 1, s));
+  std::vector<int> ga((size_t)M * B, 0);
+  std::vector<uint32_t> gth((size_t)M * B, 0);
+  for (int r = 0; r < Dt; ++r) {
+    const int base = 1 << r, nsub = 1 << r;
+    uint32_t* hist;
+    const size_t hb = sizeof(uint32_t) * (size_t)M * nsub * K;
+    DEOCT_TRY(scratch_get(ctx, SL_MH_SUBHIST, hb, (void**)&hist));
+    DEOCT_CUDA_TRY(cudaMemsetAsync(hist, 0, hb, s));
+    sub_hist_kernel<<<(unsigned)((c.npad + 255) / 256), 256, 0, s>>>(c.pos_slot, sub_of, c.clabels, c.npad,
+                                                                     base, nsub, K, hist);
+    count_launch(ctx);
+    DEOCT_TRY(check_launch("sub_hist_kernel"));
+    std::vector<uint32_t> hh;
+    DEOCT_TRY(download(ctx, hist, (size_t)M * nsub * K, &hh, s));
+    Compacted c2;
+    std::vector<int32_t> slot2((size_t)M * nsub, -1);
+    std::vector<int> pair_of;
+    int64_t off = 0;
+    for (int m = 0; m < M; ++m)
+      for (int k = 0; k < nsub; ++k) {
+        int64_t nt = 0;
+        int ncls = 0;
+        for (int y = 0; y < K; ++y) {
+          const uint32_t v = hh[((size_t)m * nsub + k) * K + y];
+          nt += v;
+          ncls += v > 0 ? 1 : 0;
+        }
+        if (nt > prm->n_min && ncls > 1) {
+          slot2[(size_t)m * nsub + k] = (int32_t)pair_of.size();
+          pair_of.push_back(m * nsub + k);
+          c2.seg_off.push_back(off);
+          c2.counts.push_back(nt);
+          off += round_up(nt, kSegAlign);
+        }
+      }
+    std::vector<uint32_t> packed((size_t)M * nsub, 0);
+    if (!pair_of.empty()) {
+      c2.npad = std::max<int64_t>(off, kSegAlign);
+      const int M2 = (int)pair_of.size();
+      int32_t *dslot2, *dcur;
+      int64_t* dseg2;
+      DEOCT_TRY(upload(ctx, SL_MH_SEG, slot2, &dslot2, s));
+      DEOCT_TRY(upload(ctx, SL_MH_STATS, c2.seg_off, &dseg2, s));
+      DEOCT_TRY(scratch_get(ctx, SL_MH_CURSOR, sizeof(int32_t) * M2, (void**)&dcur));
+      DEOCT_CUDA_TRY(cudaMemsetAsync(dcur, 0, sizeof(int32_t) * M2, s));
+      DEOCT_TRY(scratch_get(ctx, SL_MH_IDX2, sizeof(int32_t) * c2.npad, (void**)&c2.idx));
+      DEOCT_TRY(scratch_get(ctx, SL_MH_POS2, sizeof(int32_t) * c2.npad, (void**)&c2.pos_slot));
+      DEOCT_TRY(launch_fill(ctx, c2.idx, c2.npad, -1, s));
+      DEOCT_TRY(launch_fill(ctx, c2.pos_slot, c2.npad, -1, s));
+      sub_compact_kernel<<<(unsigned)((c.npad + 255) / 256), 256, 0, s>>>(
+          c.pos_slot, sub_of, c.idx, c.npad, base, nsub, dslot2, dseg2, dcur, c2.idx, c2.pos_slot);
+      count_launch(ctx);
+      DEOCT_TRY(check_launch("sub_compact_kernel"));
+      DEOCT_TRY(gather_compacted(ctx, ds, &c2, s, SL_MH_RANKS2, SL_MH_LABELS2));
+      std::vector<uint16_t> ra;
+      std::vector<uint32_t> rth;
+      std::vector<double> rf;
+      DEOCT_TRY(depth1_segments(ctx, ds, c2, 0, M2, prm->n_min, prm->alpha, &ra, &rth, &rf, s));
+      for (int j = 0; j < M2; ++j) {
+        const int m = pair_of[j] / nsub, k = pair_of[j] % nsub;
+        const int t = base + k;  // subtree node (1-based)
+        ga[(size_t)m * B + t - 1] = ra[j];
+        gth[(size_t)m * B + t - 1] = rth[j];
+        packed[pair_of[j]] = ra[j] == 0 ? 0u : ((uint32_t)(ra[j] - 1) << 24) | (rth[j] & kThetaMask);
+      }
+    }
+    if (r + 1 < Dt) {
+      uint32_t* dpk;
+      DEOCT_TRY(upload(ctx, SL_MH_CURSOR, packed, &dpk, s));
+      const unsigned grid = (unsigned)((c.npad + 255) / 256);
+      if (ds->rank_bytes == 2)
+        sub_route_kernel<uint16_t><<<grid, 256, 0, s>>>(c.pos_slot, sub_of, c.idx,
+                                                       static_cast<const uint16_t*>(ds->ranks), ds->ld,
+                                                       c.npad, base, nsub, dpk);
+      else
+        sub_route_kernel<uint32_t><<<grid, 256, 0, s>>>(c.pos_slot, sub_of, c.idx,
+                                                       static_cast<const uint32_t*>(ds->ranks), ds->ld,
+                                                       c.npad, base, nsub, dpk);
+      count_launch(ctx);
+      DEOCT_TRY(check_launch("sub_route_kernel"));
+    }
+  }
+  // genes of the greedy subtrees
+  std::vector<uint32_t> nu;
+  DEOCT_TRY(download(ctx, ds->n_unique, (size_t)ds->F, &nu, s));
+  std::vector<float> genes((size_t)M * 2 * B);
+  for (int m = 0; m < M; ++m)
+    for (int t = 0; t < B; ++t) {
+      const int a = ga[(size_t)m * B + t];
+      const uint32_t th = gth[(size_t)m * B + t];
+      encode_node_genes(a, th, a > 0 ? nu[a - 1] : 1u, &genes[(size_t)m * 2 * B + t],
+                        &genes[(size_t)m * 2 * B + B + t]);
+    }
+  DEOCT_TRY(upload(ctx, SL_MH_SEEDS, genes, d_seeds, s));
   return DEOCT_OK;
 }
 
@@ -810,8 +999,10 @@ int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uin
       int kd;
       if (Dt >= 2) {
         kd = 2;
-        if (batched) DEOCT_TRY(de_batched(ctx, ds, c, solved, Dt, prm, &ra, &rth, &rf, s));
-        else DEOCT_TRY(de_plain(ctx, ds, c, solved, Dt, prm, &ra, &rth, &rf, s));
+        float* seeds = nullptr;
+        if (prm->flags & DEOCT_CART_SEEDS) DEOCT_TRY(greedy_seeds(ctx, ds, c, Dt, prm, &seeds, s));
+        if (batched) DEOCT_TRY(de_batched(ctx, ds, c, solved, Dt, prm, seeds, &ra, &rth, &rf, s));
+        else DEOCT_TRY(de_plain(ctx, ds, c, solved, Dt, prm, seeds, &ra, &rth, &rf, s));
       } else {
         kd = 1;
         if (batched) {

@@ -25,6 +25,7 @@ DEOCT_ERR_TIMEOUT = -4
 DEOCT_ERR_BUDGET = -5
 DEOCT_DITHER_M = 0x1
 DEOCT_BATCHED = 0x2
+DEOCT_CART_SEEDS = 0x4
 
 EXPORTED = [
     "deoct_create", "deoct_destroy", "deoct_last_error_string", "deoct_version",

@@ -128,3 +128,22 @@ def test_moving_horizon_workload2_batched_equals_plain(c):
     np.testing.assert_array_equal(outs[1]["a"].astype(np.int32), ref["a"])
     np.testing.assert_array_equal(outs[1]["theta"], ref["theta"])
     np.testing.assert_array_equal(outs[1]["leaf_class"], ref["leaf_class"])
+
+
+@pytest.mark.parametrize("name", ["w0_d3h2", "w2_small", "k3_d4h3_nmin"])
+@pytest.mark.parametrize("batched", [False, True])
+def test_moving_horizon_cart_seeds_bit_exact(c, name, batched):
+    """CART warm starts (Algorithm 2): each DEOCT subtree starts with its greedy tree."""
+    from paper_2311_06952_gb300 import deoct
+    X, y, K, kw, rb = _mh_case(name)
+    ds = gpu_dataset(c, X, y, K, rb)
+    ranks, nu = oracle.encode(X)
+    ref = oracle.mh(ranks, nu, y, K, depth=kw["depth"], horizon=kw["horizon"], P=kw["P"], G=kw["G"],
+                    seed=kw["seed"], n_min=kw.get("n_min", 1), alpha=kw.get("alpha", 0.0), cart_seeds=True)
+    flags = deoct.DEOCT_CART_SEEDS | (deoct.DEOCT_BATCHED if batched else 0)
+    prm = deoct.make_params(kw["depth"], kw["P"], kw["G"], seed=kw["seed"], horizon=kw["horizon"],
+                            n_min=kw.get("n_min", 1), alpha=kw.get("alpha", 0.0), flags=flags)
+    out = deoct.deoct_fit_moving_horizon(c, ds, prm)
+    for k in ("kind", "theta", "node_fit", "leaf_class"):
+        np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+    np.testing.assert_array_equal(out["a"].astype(np.int32), ref["a"])

@@ -520,3 +520,40 @@ def test_split_values_definition():
     b = oracle.split_values(X, np.array([1, 1, 1, 0]), np.array([0, 1, 3, 0], np.uint32))
     # sorted distinct values 1, 2, 3, 7
     assert list(b) == [1.0, 1.5, 5.0, 0.0]
+
+
+
+# --------------------------------------------------------------------------
+# CART warm starts (Algorithm 2): the greedy subtree
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_greedy_tree_is_the_float_greedy_tree(seed):
+    rng = _rng(90 + seed)
+    n, F, K, D = 80, 3, 3, 3
+    X = rng.integers(0, 6, size=(n, F)).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    a, th = oracle.greedy_tree(ranks, nu, y, K, D)
+    a_ref, t_ref = _greedy_float_tree(X, y, K, D, n_min=1)
+    np.testing.assert_array_equal(a, a_ref)
+    np.testing.assert_array_equal(th, t_ref)
+    # on a subset: the greedy tree of the materialised subset
+    idx = np.sort(rng.choice(n, 50, replace=False)).astype(np.int32)
+    a1, t1 = oracle.greedy_tree(ranks, nu, y, K, D, idx=idx)
+    a2, t2 = _greedy_float_tree(X[idx], y[idx], K, D, n_min=1)
+    # thresholds are global ranks: compare the splits through the float route instead
+    np.testing.assert_array_equal(a1, a2)
+
+
+def test_cart_seed_genes_decode_to_the_greedy_tree():
+    w = datagen.make_workload(0, n=400)
+    ranks, nu = oracle.encode(w["X"])
+    out = oracle.mh(ranks, nu, w["y"], 2, depth=3, horizon=3, P=8, G=0, cart_seeds=True)
+    a, th = oracle.greedy_tree(ranks, nu, w["y"], 2, 3)
+    # with G = 0 the root keeps the best initial individual; the greedy tree is slot 0,
+    # so the root's fitness is at most the greedy tree's fitness
+    counts = oracle.eval_counts(ranks, w["y"], 2, a[None], th[None], 3)
+    f, _, _, _ = oracle.fitness(counts, a[None], 400)
+    assert out["node_fit"][0] <= f[0]
+    assert out["kind"][0] == 2
