@@ -52,6 +52,7 @@ typedef enum {
 #define DEOCT_DITHER_M 0x1u /* M = rand(0,1) per (generation, individual), Section 3.3 */
 #define DEOCT_BATCHED 0x2u  /* moving horizon: one batched launch per level */
 #define DEOCT_CART_SEEDS 0x4u /* moving horizon: seed each DEOCT subtree with its greedy tree */
+#define DEOCT_DE_SEEDS 0x8u   /* moving horizon: seed each DEOCT subtree from a full-depth DEOCT */
 
 typedef struct deoct_ctx deoct_ctx;
 
@@ -233,6 +234,11 @@ DEOCT_API int deoct_fit_subtree(deoct_ctx* ctx, const deoct_dataset* ds, const i
  * depth D_t on X_t (the depth-1 search applied top-down inside the subtree,
  * same solve rule and tie order), encoded as genes a + 1/2 and the float32
  * bhat nearest to (theta + 1/2)/(n_p + 1) that decodes to theta.
+ * DEOCT_DE_SEEDS adds the DEOCT warm start of Algorithm 2: one DEOCT of the
+ * full depth D on the whole set (Philox stream 0) runs first, and the subtree
+ * of its best tree at node t (same shape and location) seeds node t's DEOCT.
+ * With both flags the seeds are, in order, the DEOCT subtree and the greedy
+ * subtree.
  *  a_out [2^D - 1] uint16, theta_out [2^D - 1] uint32, leaf_class_out [2^D]
  *  uint8 (Eq. opt_c on the whole set, lowest class on ties): host arrays.
  *  kind_out [2^D - 1] int32 (0 artificial, 1 depth-1 search, 2 DEOCT) and

@@ -63,7 +63,8 @@ class MHParams(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("horizon", ctypes.c_int32), ("P", ctypes.c_int32),
                 ("G", ctypes.c_int32), ("M", ctypes.c_float), ("CR", ctypes.c_float),
                 ("alpha", ctypes.c_double), ("n_min", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("dither", ctypes.c_int32), ("cart_seeds", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("dither", ctypes.c_int32), ("cart_seeds", ctypes.c_int32),
+                ("de_seeds", ctypes.c_int32)]
 
 
 def lib():
@@ -253,14 +254,15 @@ def greedy_tree(ranks, n_unique, y, K, depth, idx=None, n_min=1, alpha=0.0):
 
 
 def mh(ranks, n_unique, y, K, depth, horizon, P, G, M=0.5, CR=0.9, alpha=0.0, n_min=1, seed=0,
-       dither=False, cart_seeds=False):
+       dither=False, cart_seeds=False, de_seeds=False):
     """Algorithm 2 (moving-horizon DEOCT): dict(a, theta, leaf_class, kind, node_fit)."""
     ranks = _c(ranks, np.uint32)
     nu = _c(n_unique, np.uint32)
     y = _c(y, np.uint8)
     F, n = ranks.shape
     B = (1 << depth) - 1
-    prm = MHParams(depth, horizon, P, G, M, CR, alpha, n_min, seed, int(dither), int(cart_seeds))
+    prm = MHParams(depth, horizon, P, G, M, CR, alpha, n_min, seed, int(dither), int(cart_seeds),
+                   int(de_seeds))
     a = np.empty(B, np.int32)
     th = np.empty(B, np.uint32)
     lc = np.empty(1 << depth, np.uint8)

@@ -475,7 +475,8 @@ typedef struct {
   int32_t n_min;
   uint64_t seed;
   int32_t dither;
-  int32_t cart_seeds; /* 1: CART warm start in slot 0 of every DEOCT subtree */
+  int32_t cart_seeds; /* 1: CART warm start of every DEOCT subtree */
+  int32_t de_seeds;   /* 1: warm start from a full-depth DEOCT (Philox stream 0) */
 } orc_mh_params;
 
 /* Greedy misclassification tree of depth D on the samples idx[0..n_sub-1]
@@ -557,6 +558,28 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
   if (!sub || !seen) { free(sub); free(seen); return ORC_ERR_OOM; }
   for (int32_t t = 0; t < B; ++t) { a_out[t] = 0; theta_out[t] = 0; }
   int rc = ORC_OK;
+  /* DEOCT warm start trees {(a, b)}^0 of Algorithm 2: the best tree of one
+   * DEOCT of the full depth on the whole set */
+  int32_t* wa = NULL;
+  uint32_t* wth = NULL;
+  if (prm->de_seeds && D >= 2 && prm->horizon >= 2) {
+    orc_de_params fp;
+    fp.depth = D; fp.P = prm->P; fp.G = prm->G; fp.M = prm->M; fp.CR = prm->CR;
+    fp.alpha = prm->alpha; fp.n_min = prm->n_min; fp.seed = prm->seed; fp.stream = 0;
+    fp.dither = prm->dither;
+    float* fpop = (float*)malloc((size_t)prm->P * 2 * B * sizeof(float));
+    double* ffit = (double*)malloc((size_t)prm->P * sizeof(double));
+    wa = (int32_t*)malloc((size_t)B * sizeof(int32_t));
+    wth = (uint32_t*)malloc((size_t)B * sizeof(uint32_t));
+    if (!fpop || !ffit || !wa || !wth) rc = ORC_ERR_OOM;
+    int32_t fbest = 0;
+    if (rc == ORC_OK)
+      rc = orc_de_run(ranks, n, F, n_unique, y, K, NULL, n, &fp, NULL, 0, fpop, ffit, &fbest, NULL,
+                      NULL, NULL);
+    if (rc == ORC_OK) orc_decode(fpop + (int64_t)fbest * 2 * B, 1, D, F, n_unique, wa, wth);
+    free(fpop);
+    free(ffit);
+  }
   for (int32_t t = 1; t <= B && rc == ORC_OK; ++t) {
     int32_t d = 0;
     while ((1 << (d + 1)) <= t) ++d;
@@ -587,7 +610,7 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
       int32_t Bt = (1 << Dt) - 1;
       float* pop = (float*)malloc((size_t)prm->P * 2 * Bt * sizeof(float));
       double* fit = (double*)malloc((size_t)prm->P * sizeof(double));
-      float* seed_genes = (float*)malloc((size_t)2 * Bt * sizeof(float));
+      float* seed_genes = (float*)malloc((size_t)2 * 2 * Bt * sizeof(float));
       int32_t* ga = (int32_t*)malloc((size_t)Bt * sizeof(int32_t));
       uint32_t* gth = (uint32_t*)malloc((size_t)Bt * sizeof(uint32_t));
       if (!pop || !fit || !seed_genes || !ga || !gth) {
@@ -596,13 +619,23 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
         break;
       }
       int32_t S = 0;
-      if (prm->cart_seeds) {
+      if (wa) { /* the warm-start tree's subtree with the same shape and location */
+        float* g = seed_genes + (int64_t)S * 2 * Bt;
+        for (int32_t r = 0, q = 0; r < Dt; ++r)
+          for (int32_t j = 0; j < (1 << r); ++j, ++q) {
+            int32_t gt = (t << r) + j;
+            node_genes(wa[gt - 1], wth[gt - 1], wa[gt - 1] > 0 ? n_unique[wa[gt - 1] - 1] : 1u,
+                       &g[q], &g[Bt + q]);
+          }
+        S += 1;
+      }
+      if (prm->cart_seeds) { /* the CART solution of the subtree */
+        float* g = seed_genes + (int64_t)S * 2 * Bt;
         rc = orc_greedy_tree(ranks, n, F, n_unique, y, K, sub, nt, Dt, prm->n_min, prm->alpha, ga,
                              gth);
         for (int32_t q = 0; q < Bt && rc == ORC_OK; ++q)
-          node_genes(ga[q], gth[q], ga[q] > 0 ? n_unique[ga[q] - 1] : 1u, &seed_genes[q],
-                     &seed_genes[Bt + q]);
-        S = 1;
+          node_genes(ga[q], gth[q], ga[q] > 0 ? n_unique[ga[q] - 1] : 1u, &g[q], &g[Bt + q]);
+        S += 1;
       }
       int32_t best = 0;
       if (rc == ORC_OK)
@@ -637,6 +670,8 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
       }
     }
   }
+  free(wa);
+  free(wth);
   if (rc == ORC_OK) {
     uint32_t* counts = (uint32_t*)malloc((size_t)L * K * sizeof(uint32_t));
     if (!counts) rc = ORC_ERR_OOM;

@@ -485,7 +485,7 @@ uint64_t tune_key(int W, int D, int F, int K, int P, int64_t npad, int M) {
 // step launch per generation, replayed from a captured CUDA graph.
 int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
                const std::vector<int>& node_ids, int Dt, const deoct_params* prm,
-               const float* d_seeds, std::vector<uint16_t>* ra, std::vector<uint32_t>* rth,
+               const float* d_seeds, int S, std::vector<uint16_t>* ra, std::vector<uint32_t>* rth,
                std::vector<double>* rf, cudaStream_t s) {
   const int M = (int)node_ids.size();
   const int P = prm->pop, B = (1 << Dt) - 1, L = 1 << Dt, m2 = 2 * B, K = ds->K, F = ds->F;
@@ -517,10 +517,10 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     d.nodes = reinterpret_cast<uint32_t*>(take((size_t)P * B * 4));
     d.counts = reinterpret_cast<uint32_t*>(take((size_t)P * L * K * 4));
     d.n_unique = ds->n_unique;
-    d.seeds = d_seeds ? d_seeds + (size_t)m * m2 : nullptr;
+    d.seeds = (d_seeds && S > 0) ? d_seeds + (size_t)m * S * m2 : nullptr;
     d.n_valid = c.counts[m];
     d.stream_id = (uint64_t)node_ids[m];
-    d.S = d_seeds ? 1 : 0;
+    d.S = d.seeds ? S : 0;
     d.F = F;
     d.K = K;
     EvalProb& e = be.probs[m];
@@ -678,7 +678,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
 // Plain form: one DEOCT (own launches) per node segment.
 int de_plain(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
              const std::vector<int>& node_ids, int Dt, const deoct_params* prm, const float* d_seeds,
-             std::vector<uint16_t>* ra, std::vector<uint32_t>* rth, std::vector<double>* rf,
+             int S, std::vector<uint16_t>* ra, std::vector<uint32_t>* rth, std::vector<double>* rf,
              cudaStream_t s) {
   const int M = (int)node_ids.size();
   const int P = prm->pop, B = (1 << Dt) - 1;
@@ -700,8 +700,8 @@ int de_plain(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   rf->resize(M);
   for (int m = 0; m < M; ++m) {
     deoct_dataset v = segment_view(ds, c, m);
-    const float* sd = d_seeds ? d_seeds + (size_t)m * 2 * B : nullptr;
-    DEOCT_TRY(run_deoct(ctx, &v, nullptr, v.n, &dp, (uint64_t)node_ids[m], sd, sd ? 1 : 0, pop, fit,
+    const float* sd = (d_seeds && S > 0) ? d_seeds + (size_t)m * S * 2 * B : nullptr;
+    DEOCT_TRY(run_deoct(ctx, &v, nullptr, v.n, &dp, (uint64_t)node_ids[m], sd, sd ? S : 0, pop, fit,
                         best, s));
     DEOCT_TRY(launch_best_extract(ctx, pop, fit, best, Dt, ds->F, ds->n_unique, da, dth, df, s));
     std::vector<double> hf;
@@ -799,7 +799,7 @@ void encode_node_genes(int a, uint32_t theta, uint32_t np, float* ahat, float* b
 // Algorithm 2): per subtree depth r, solved (segment, node) pairs get the
 // exhaustive depth-1 split of their samples.  Result: genes [M][2B] (device).
 int greedy_seeds(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c, int Dt,
-                 const deoct_params* prm, float** d_seeds, cudaStream_t s) {
+                 const deoct_params* prm, std::vector<float>* out_genes, cudaStream_t s) {
   const int M = (int)c.counts.size();
   const int B = (1 << Dt) - 1, K = ds->K;
   int32_t* sub_of;
@@ -898,7 +898,7 @@ int greedy_seeds(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c, in
       encode_node_genes(a, th, a > 0 ? nu[a - 1] : 1u, &genes[(size_t)m * 2 * B + t],
                         &genes[(size_t)m * 2 * B + B + t]);
     }
-  DEOCT_TRY(upload(ctx, SL_MH_SEEDS, genes, d_seeds, s));
+  *out_genes = std::move(genes);
   return DEOCT_OK;
 }
 
@@ -946,6 +946,31 @@ int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uin
   DEOCT_TRY(scratch_get(ctx, SL_MH_NODEOF, sizeof(int32_t) * n, (void**)&node_of));
   DEOCT_TRY(scratch_get(ctx, SL_MH_HOSTBUF, sizeof(uint32_t) * (size_t)(2 * Lf) * K + 64, (void**)&hist));
   DEOCT_TRY(launch_fill(ctx, node_of, n, 1, s));
+  // DEOCT warm start (Algorithm 2): one DEOCT of the full depth on the whole set
+  std::vector<int> full_a;
+  std::vector<uint32_t> full_th, nu_host;
+  DEOCT_TRY(download(ctx, ds->n_unique, (size_t)ds->F, &nu_host, s));
+  if ((prm->flags & DEOCT_DE_SEEDS) && D >= 2 && H >= 2) {
+    deoct_params fp = *prm;
+    fp.depth = D;
+    float* pop;
+    double* fit;
+    int32_t* best;
+    DEOCT_TRY(scratch_get(ctx, SL_POP, (size_t)prm->pop * 2 * B * 4, (void**)&pop));
+    DEOCT_TRY(scratch_get(ctx, SL_FIT, (size_t)prm->pop * 8, (void**)&fit));
+    DEOCT_TRY(scratch_get(ctx, SL_BEST, 64, (void**)&best));
+    DEOCT_TRY(run_deoct(ctx, ds, nullptr, n, &fp, 0, nullptr, 0, pop, fit, best, s));
+    unsigned char* dres;
+    DEOCT_TRY(scratch_get(ctx, SL_D1_RESULT, (size_t)B * 6 + 64, (void**)&dres));
+    double* df = reinterpret_cast<double*>(dres);
+    uint32_t* dth = reinterpret_cast<uint32_t*>(dres + 8);
+    uint16_t* da = reinterpret_cast<uint16_t*>(dres + 8 + (size_t)B * 4);
+    DEOCT_TRY(launch_best_extract(ctx, pop, fit, best, D, ds->F, ds->n_unique, da, dth, df, s));
+    std::vector<uint16_t> ha;
+    DEOCT_TRY(download(ctx, dth, (size_t)B, &full_th, s));
+    DEOCT_TRY(download(ctx, da, (size_t)B, &ha, s));
+    full_a.assign(ha.begin(), ha.end());
+  }
   const int64_t npad_max = round_up(n + (int64_t)kSegAlign * (Lf / 2), 64);
   Compacted c;
   DEOCT_TRY(scratch_get(ctx, SL_MH_IDX, sizeof(int32_t) * npad_max, (void**)&c.idx));
@@ -999,10 +1024,35 @@ int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uin
       int kd;
       if (Dt >= 2) {
         kd = 2;
+        // warm starts of Algorithm 2, per node in this order: the subtree of the
+        // full-depth DEOCT at the node's location, then the greedy (CART) subtree
+        const int Bt = (1 << Dt) - 1;
+        const bool de_ws = !full_a.empty(), cart_ws = (prm->flags & DEOCT_CART_SEEDS) != 0;
+        const int S = (de_ws ? 1 : 0) + (cart_ws ? 1 : 0);
         float* seeds = nullptr;
-        if (prm->flags & DEOCT_CART_SEEDS) DEOCT_TRY(greedy_seeds(ctx, ds, c, Dt, prm, &seeds, s));
-        if (batched) DEOCT_TRY(de_batched(ctx, ds, c, solved, Dt, prm, seeds, &ra, &rth, &rf, s));
-        else DEOCT_TRY(de_plain(ctx, ds, c, solved, Dt, prm, seeds, &ra, &rth, &rf, s));
+        if (S > 0) {
+          std::vector<float> cart;
+          if (cart_ws) DEOCT_TRY(greedy_seeds(ctx, ds, c, Dt, prm, &cart, s));
+          std::vector<float> all((size_t)M * S * 2 * Bt);
+          for (int m = 0; m < M; ++m) {
+            float* dst = &all[(size_t)m * S * 2 * Bt];
+            if (de_ws) {
+              const int t = solved[m];
+              for (int r = 0, q = 0; r < Dt; ++r)
+                for (int j = 0; j < (1 << r); ++j, ++q) {
+                  const int gt = (t << r) + j;  // global BFS index of subtree node q + 1
+                  const int av = full_a[gt - 1];
+                  encode_node_genes(av, full_th[gt - 1], av > 0 ? nu_host[av - 1] : 1u, &dst[q],
+                                    &dst[Bt + q]);
+                }
+              dst += 2 * Bt;
+            }
+            if (cart_ws) memcpy(dst, &cart[(size_t)m * 2 * Bt], sizeof(float) * 2 * Bt);
+          }
+          DEOCT_TRY(upload(ctx, SL_MH_SEEDS, all, &seeds, s));
+        }
+        if (batched) DEOCT_TRY(de_batched(ctx, ds, c, solved, Dt, prm, seeds, S, &ra, &rth, &rf, s));
+        else DEOCT_TRY(de_plain(ctx, ds, c, solved, Dt, prm, seeds, S, &ra, &rth, &rf, s));
       } else {
         kd = 1;
         if (batched) {

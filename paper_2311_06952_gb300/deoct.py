@@ -26,6 +26,7 @@ DEOCT_ERR_BUDGET = -5
 DEOCT_DITHER_M = 0x1
 DEOCT_BATCHED = 0x2
 DEOCT_CART_SEEDS = 0x4
+DEOCT_DE_SEEDS = 0x8
 
 EXPORTED = [
     "deoct_create", "deoct_destroy", "deoct_last_error_string", "deoct_version",

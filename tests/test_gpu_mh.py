@@ -147,3 +147,24 @@ def test_moving_horizon_cart_seeds_bit_exact(c, name, batched):
     for k in ("kind", "theta", "node_fit", "leaf_class"):
         np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
     np.testing.assert_array_equal(out["a"].astype(np.int32), ref["a"])
+
+
+@pytest.mark.parametrize("name", ["w0_d3h2", "k3_d4h3_nmin"])
+@pytest.mark.parametrize("both", [False, True])
+def test_moving_horizon_deoct_seeds_bit_exact(c, name, both):
+    """DEOCT warm starts (Algorithm 2): each subtree starts from the full-depth DEOCT's subtree at
+    its location (and, with both flags, also from its greedy tree)."""
+    from paper_2311_06952_gb300 import deoct
+    X, y, K, kw, rb = _mh_case(name)
+    ds = gpu_dataset(c, X, y, K, rb)
+    ranks, nu = oracle.encode(X)
+    ref = oracle.mh(ranks, nu, y, K, depth=kw["depth"], horizon=kw["horizon"], P=kw["P"], G=kw["G"],
+                    seed=kw["seed"], n_min=kw.get("n_min", 1), alpha=kw.get("alpha", 0.0),
+                    cart_seeds=both, de_seeds=True)
+    flags = deoct.DEOCT_DE_SEEDS | deoct.DEOCT_BATCHED | (deoct.DEOCT_CART_SEEDS if both else 0)
+    prm = deoct.make_params(kw["depth"], kw["P"], kw["G"], seed=kw["seed"], horizon=kw["horizon"],
+                            n_min=kw.get("n_min", 1), alpha=kw.get("alpha", 0.0), flags=flags)
+    out = deoct.deoct_fit_moving_horizon(c, ds, prm)
+    for k in ("kind", "theta", "node_fit", "leaf_class"):
+        np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+    np.testing.assert_array_equal(out["a"].astype(np.int32), ref["a"])

@@ -557,3 +557,18 @@ def test_cart_seed_genes_decode_to_the_greedy_tree():
     f, _, _, _ = oracle.fitness(counts, a[None], 400)
     assert out["node_fit"][0] <= f[0]
     assert out["kind"][0] == 2
+
+
+def test_deoct_warm_start_bounds_the_root():
+    """With G = 0 the root of MH keeps the best initial individual, and the full-depth
+    DEOCT's root subtree is one of them (Algorithm 2, DEOCT warm start)."""
+    w = datagen.make_workload(0, n=400)
+    ranks, nu = oracle.encode(w["X"])
+    full = oracle.de_run(ranks, nu, w["y"], 2, depth=3, P=8, G=0, seed=2, stream=0)
+    a, th = oracle.decode(full["pop"][full["best"]][None], 3, nu)
+    # the depth-2 subtree at the root of the full tree
+    sub_a, sub_t = a[:, :3], th[:, :3]
+    counts = oracle.eval_counts(ranks, w["y"], 2, sub_a, sub_t, 2)
+    f, _, _, _ = oracle.fitness(counts, sub_a, 400)
+    out = oracle.mh(ranks, nu, w["y"], 2, depth=3, horizon=2, P=8, G=0, seed=2, de_seeds=True)
+    assert out["kind"][0] == 2 and out["node_fit"][0] <= f[0]
