@@ -211,11 +211,51 @@ int run_deoct(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* idx, int64
   DEArgs a = de_args(ds, p, n_sub, stream_id, b, pop, fit, best, seeds, S, ctx->d_status);
   DEOCT_TRY(de_launch_init(ctx, a, s));
   DEOCT_TRY(eval_single(ctx, ds, idx, n_sub, b.nodes, b.counts, p->pop, p->depth, s));
-  DEOCT_TRY(de_launch_step(ctx, a, 1, DE_FIRST | (p->gens >= 1 ? DE_TRIAL : 0), s));
-  for (int g = 1; g <= p->gens; ++g) {
-    DEOCT_TRY(eval_single(ctx, ds, idx, n_sub, b.nodes, b.counts, p->pop, p->depth, s));
-    DEOCT_TRY(de_launch_step(ctx, a, g + 1, DE_SELECT | (g < p->gens ? DE_TRIAL : 0), s));
+  // The generation number lives on the device (set to 1 by the init kernel and
+  // advanced by every trial step), so every generation is the same pair of
+  // launches: captured once as a CUDA graph and replayed G times.  With
+  // per-launch timing on, the launches are issued directly so that each
+  // evaluator launch gets its own events.
+  DEOCT_TRY(de_launch_step(ctx, a, 0, DE_FIRST | DE_GEN_DEVICE | (p->gens >= 1 ? DE_TRIAL : 0), s));
+  if (p->gens < 1) return DEOCT_OK;
+  if (ctx->timing || p->gens < 3) {
+    for (int g = 1; g <= p->gens; ++g) {
+      DEOCT_TRY(eval_single(ctx, ds, idx, n_sub, b.nodes, b.counts, p->pop, p->depth, s));
+      DEOCT_TRY(de_launch_step(ctx, a, 0, DE_SELECT | DE_TRIAL | DE_GEN_DEVICE, s));
+    }
+    return DEOCT_OK;
   }
+  if (!ctx->cap_stream)
+    DEOCT_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  const uint64_t l0 = ctx->launches, e0 = ctx->eval_launches;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DEOCT_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = eval_single(ctx, ds, idx, n_sub, b.nodes, b.counts, p->pop, p->depth, ctx->cap_stream);
+  if (rc == DEOCT_OK) rc = de_launch_step(ctx, a, 0, DE_SELECT | DE_TRIAL | DE_GEN_DEVICE, ctx->cap_stream);
+  cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  const uint64_t per_launch = ctx->launches - l0, per_eval = ctx->eval_launches - e0;
+  ctx->launches = l0;
+  ctx->eval_launches = e0;
+  if (rc != DEOCT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ce != cudaSuccess) return set_error(DEOCT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return set_error(DEOCT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+  }
+  for (int g = 1; g <= p->gens && ce == cudaSuccess; ++g) {
+    ce = cudaGraphLaunch(exec, s);
+    ctx->launches += per_launch;
+    ctx->eval_launches += per_eval;
+  }
+  // the graph may be destroyed once its launches are queued
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return set_error(DEOCT_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(ce));
   return DEOCT_OK;
 }
 

@@ -20,10 +20,12 @@ PRESETS = {
 
 class MHDEOCTClassifier:
     """Moving-horizon DEOCT (Algorithm 2).  ``horizon >= depth`` is plain DEOCT
-    of the whole tree at the root, kept node by node."""
+    of the whole tree at the root, kept node by node.  ``warm_starts`` selects
+    the warm starts of Algorithm 2 ("cart", "deoct"; the paper uses both)."""
 
     def __init__(self, depth=3, horizon=None, preset="normal", pop=None, gens=None, cr=None, mut_f=None,
-                 dither=None, alpha=0.0, n_min=1, seed=0, batched=True, device=0):
+                 dither=None, alpha=0.0, n_min=1, seed=0, batched=True, warm_starts=("cart", "deoct"),
+                 device=0):
         p = dict(PRESETS[preset])
         for k, v in dict(pop=pop, gens=gens, cr=cr, mut_f=mut_f, dither=dither).items():
             if v is not None:
@@ -33,6 +35,7 @@ class MHDEOCTClassifier:
         self.params = p
         self.alpha, self.n_min, self.seed = float(alpha), int(n_min), int(seed)
         self.batched = bool(batched)
+        self.warm_starts = tuple(warm_starts or ())  # Algorithm 2: CART and DEOCT warm starts
         self.device = device
         self.tree_ = None
         self._ctx = None
@@ -63,7 +66,9 @@ class MHDEOCTClassifier:
         ranks, nu, uniq = deoct.deoct_encode_ex(ctx, Xd, rank_bytes)
         ds = deoct.DeviceDataset(ranks, rank_bytes, nu, yd, n, F, K)
         flags = (deoct.DEOCT_BATCHED if self.batched else 0) | \
-            (deoct.DEOCT_DITHER_M if self.params["dither"] else 0)
+            (deoct.DEOCT_DITHER_M if self.params["dither"] else 0) | \
+            (deoct.DEOCT_CART_SEEDS if "cart" in self.warm_starts else 0) | \
+            (deoct.DEOCT_DE_SEEDS if "deoct" in self.warm_starts else 0)
         prm = deoct.make_params(self.depth, self.params["pop"], self.params["gens"],
                                 mut_f=self.params["mut_f"], cr=self.params["cr"], alpha=self.alpha,
                                 n_min=self.n_min, seed=self.seed, horizon=self.horizon, flags=flags)

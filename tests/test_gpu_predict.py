@@ -68,7 +68,8 @@ def test_split_values_and_predict_bit_exact(c):
 def test_estimator_training_accuracy_is_the_loss_identity(c):
     from paper_2311_06952_gb300.estimator import MHDEOCTClassifier
     w = datagen.make_workload(0)
-    clf = MHDEOCTClassifier(depth=3, horizon=2, pop=32, gens=20, cr=0.9, dither=False, seed=0).fit(w["X"], w["y"])
+    clf = MHDEOCTClassifier(depth=3, horizon=2, pop=32, gens=20, cr=0.9, dither=False, seed=0,
+                            warm_starts=None).fit(w["X"], w["y"])
     tr = clf.tree_
     # the oracle's errors of the fitted tree on the training set
     ranks, nu = oracle.encode(w["X"])
@@ -84,3 +85,16 @@ def test_estimator_training_accuracy_is_the_loss_identity(c):
     ref = oracle.mh(ranks, nu, w["y"], 2, depth=3, horizon=2, P=32, G=20, CR=0.9, seed=0)
     np.testing.assert_array_equal(tr["a"].astype(np.int32), ref["a"])
     np.testing.assert_array_equal(tr["theta"], ref["theta"])
+
+
+def test_estimator_paper_defaults_run_and_match_oracle(c):
+    """Normal preset (P=100, G=600, CR=0.1, dithered M) with both warm starts."""
+    from paper_2311_06952_gb300.estimator import MHDEOCTClassifier
+    w = datagen.make_workload(0, n=600)
+    clf = MHDEOCTClassifier(depth=3, gens=60, seed=4).fit(w["X"], w["y"])
+    ranks, nu = oracle.encode(w["X"])
+    ref = oracle.mh(ranks, nu, w["y"], 2, depth=3, horizon=3, P=100, G=60, CR=0.1, seed=4, dither=True,
+                    cart_seeds=True, de_seeds=True)
+    np.testing.assert_array_equal(clf.tree_["a"].astype(np.int32), ref["a"])
+    np.testing.assert_array_equal(clf.tree_["theta"], ref["theta"])
+    np.testing.assert_array_equal(clf.tree_["leaf_class"], ref["leaf_class"])
