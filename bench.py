@@ -348,6 +348,43 @@ def eval_workload1(args):
             "ms": ms, "evals": evals, "evals_per_s": evals / (ms / 1000.0), "samples": len(times)}
 
 
+PAPER_TABLE3_S = {  # MH-DEOCT training time on an A100 (Table 3), seconds, D = 2 / 4 / 8
+    "bitcoin-heist": (77.22, 259.98, 1633.93), "susy": (164.03, 399.88, 5100.47),
+    "higgs": (333.01, 1049.87, 15885.24)}
+
+
+def run_table3(args):
+    """Time-to-train on synthetic sets shaped like the paper's large-scale sets (Table 3):
+    MH-DEOCT in the paper's Normal mode (P=100, G=600, CR=0.1, M=rand(0,1)) with CART and DEOCT
+    warm starts, horizon 2 at depth 2 and 3 otherwise, 75/25 split.  The paper's A100 times
+    are printed beside ours as context (different data of the same shape)."""
+    import torch
+    from paper_2311_06952_gb300 import build as _build
+    from paper_2311_06952_gb300 import datagen
+    from paper_2311_06952_gb300.estimator import MHDEOCTClassifier
+    _build.build()
+    rows = []
+    for name in args.table3.split(","):
+        d = datagen.table3_standin(name)
+        for di, depth in enumerate((2, 4, 8)):
+            clf = MHDEOCTClassifier(depth=depth, preset="normal", seed=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            clf.fit(d["Xtr"], d["ytr"], K=d["K"])
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            rows.append({"set": name, "shape": list(datagen.TABLE3_SHAPES[name]), "depth": depth,
+                         "train_s": t, "train_acc": clf.score(d["Xtr"], d["ytr"]),
+                         "test_acc": clf.score(d["Xte"], d["yte"]),
+                         "paper_a100_s": PAPER_TABLE3_S[name][di],
+                         "paper_time_over_ours": PAPER_TABLE3_S[name][di] / t})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "table3-shapes", "settings": "Normal mode P=100 G=600 CR=0.1 dithered M, "
+                      "CART + DEOCT warm starts, horizon 2 (D=2) / 3, 75/25 split, synthetic data of "
+                      "the paper's Table 3 shapes", "rows": rows}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -488,11 +525,14 @@ def main():
     ap.add_argument("--mh-n", type=int, default=1_000_000)
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many requests")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--table3", default="", help="comma list of bitcoin-heist,susy,higgs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.table3:
+        return run_table3(args)
     return run_ours(args)
 
 

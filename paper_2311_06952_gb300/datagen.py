@@ -174,3 +174,23 @@ def make_request_data(req):
     y = planted_tree_labels(X, req["depth"], req["K"], rng)
     y = flip_labels(y, req["K"], 0.05, rng)
     return dict(X=X, y=y)
+
+
+# Shapes of the paper's large-scale sets (Table 3): samples, features, classes.
+TABLE3_SHAPES = {"bitcoin-heist": (2_916_697, 8, 29), "susy": (5_000_000, 18, 2),
+                 "higgs": (11_000_000, 28, 2)}
+
+
+def table3_standin(name, seed=2000, train_frac=0.75):
+    """Synthetic stand-in with the shape of one of the paper's large-scale sets:
+    Gaussian-mixture features (K components), labels from a planted depth-6 tree,
+    5% flips; split 75/25 into train and test as in Section 5."""
+    N, F, K = TABLE3_SHAPES[name]
+    rng = _rng(seed + sum(name.encode()))
+    X, _ = gaussian_mixture(N, F, K, rng)
+    y = planted_tree_labels(X, 6, K, rng)
+    y = flip_labels(y, K, 0.05, rng)
+    perm = rng.permutation(N)
+    ntr = int(N * train_frac)
+    tr, te = perm[:ntr], perm[ntr:]
+    return dict(name=name, Xtr=X[tr], ytr=y[tr], Xte=X[te], yte=y[te], K=K)
