@@ -83,7 +83,7 @@ __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127)
 //   stage   [F][S] TMA landing zone (uint16 only; the uint32 path lands in `tile`)
 //   nodes   [TG][B] {shared address of the feature row, theta}
 //   aux     ballot mode: class masks [S/32][Q][32]; atomic mode: labels [S]
-//   cnt     ballot mode: job counts [TG][2^D K]; atomic mode: per-warp histograms
+//   cnt     job counts [TG][2^D K] (both modes)
 struct SmemLayout {
   size_t tile, stage, nodes, aux, cnt, total;
 };
@@ -103,7 +103,7 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(int mode, int W, int 
     s.total = s.cnt + align128((size_t)TG * LK * 4);
   } else {
     s.cnt = s.aux + align128((size_t)S);
-    s.total = s.cnt + align128((size_t)warps * LK * 4);
+    s.total = s.cnt + align128((size_t)TG * LK * 4);
   }
   return s;
 }
@@ -248,10 +248,6 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     mbar_init(&mbar, 1);
     fence_mbar_init();
   }
-  if (MODE == 1) {
-    const int LK = L * a.Kmax;
-    for (int e = threadIdx.x; e < nw * LK; e += blockDim.x) cnt_s[e] = 0;
-  }
   __syncthreads();
 
   uint32_t phase = 0;
@@ -262,12 +258,10 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   bool staged = false; // the current tile's rows are already in flight (prefetched)
 
   auto flush = [&](const JobView& v) {
-    if (MODE == 0) {
-      uint32_t* dst = v.p->counts + (int64_t)v.tree0 * LK;
-      for (int e = threadIdx.x; e < v.ntrees * LK; e += blockDim.x) {
-        uint32_t c = cnt_s[e];
-        if (c) atomicAdd(dst + e, c);
-      }
+    uint32_t* dst = v.p->counts + (int64_t)v.tree0 * LK;
+    for (int e = threadIdx.x; e < v.ntrees * LK; e += blockDim.x) {
+      uint32_t c = cnt_s[e];
+      if (c) atomicAdd(dst + e, c);
     }
   };
 
@@ -288,8 +282,8 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
         uint32_t f = pk >> 24;
         nodes_s[e] = make_uint2(tile_sa + f * (uint32_t)S * (uint32_t)W, pk & kThetaMask);
       }
+      for (int e = threadIdx.x; e < jv.ntrees * LK; e += blockDim.x) cnt_s[e] = 0;
       if (MODE == 0) {
-        for (int e = threadIdx.x; e < jv.ntrees * LK; e += blockDim.x) cnt_s[e] = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           int b = lane + 32 * q;
@@ -406,10 +400,11 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     }
 
     // ---- route + count ---------------------------------------------------
-    for (int i = warp; i < jv.ntrees; i += nw) {
-      const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
-      const uint2 n1 = nodes_s[i * B];
-      if (MODE == 0) {
+    if (MODE == 0) {
+      // ballot mode: a warp owns a tree and walks all chunk pairs of the tile
+      for (int i = warp; i < jv.ntrees; i += nw) {
+        const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
+        const uint2 n1 = nodes_s[i * B];
         uint2 n2 = n1, n3 = n1;
         if (D >= 2) {
           n2 = nodes_s[i * B + 1];
@@ -431,9 +426,14 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
           int b = lane + 32 * q;
           if (b < LK) cnt_s[i * LK + b] += cnt[q];
         }
-      } else {
-        uint32_t* hw = cnt_s + warp * (L * a.Kmax);
-        for (int c = 0; c < nch; ++c) {
+      }
+    } else {
+      // shared-atomic mode (many bins): all warps work on one tree at a time,
+      // splitting its chunks, and add into the job's shared counts
+      for (int i = 0; i < jv.ntrees; ++i) {
+        const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;
+        uint32_t* ci = cnt_s + i * LK;
+        for (int c = warp; c < nch; c += nw) {
           const uint32_t j = (uint32_t)(c * 32 + lane);
           const uint32_t jo = tile_offset<W>(j);
           uint32_t t = 1;
@@ -443,19 +443,9 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
             uint32_t rv = lds_rank<W>(nd.x + jo);
             t = 2 * t + (rv >= nd.y ? 1u : 0u);
           }
-          uint32_t y = lab_s[j];
-          if (y < (uint32_t)K) atomicAdd(hw + (t - L) * K + y, 1u);
+          const uint32_t y = lab_s[j];
+          if (y < (uint32_t)K) atomicAdd(ci + (t - L) * K + y, 1u);
         }
-        __syncwarp();
-        uint32_t* dst = P.counts + (int64_t)(jv.tree0 + i) * LK;
-        for (int b = lane; b < LK; b += 32) {
-          uint32_t v = hw[b];
-          if (v) {
-            atomicAdd(dst + b, v);
-            hw[b] = 0;
-          }
-        }
-        __syncwarp();
       }
     }
     __syncthreads();
@@ -574,36 +564,46 @@ static size_t eval_smem(int mode, int W, int D, int S, int TG, int F, int K, int
 }
 
 static int eval_mode(int D, int K) { return ((1 << D) * K <= 32 * kQMax && D <= 5) ? 0 : 1; }
+int eval_counting_mode(int D, int K) { return eval_mode(D, K); }
 
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob) {
   EvalConfig c;
   const int mode = eval_mode(D, K);
-  // measured on GB300 (n = 1e7, F = 10, depth 4, P = 1024): 16 warps per CTA and
-  // two CTAs per SM beat 8 warps by 1.5x; tiles of 1024 samples with 256 trees
-  // per job were the fastest shape that leaves room for two CTAs
-  c.S = 2048;
-  c.TG = std::min(P, 256);
-  c.warps = 16;
   const int limit = std::min(ctx->max_smem_optin, 227 * 1024);
   const size_t two_per_sm = (size_t)(ctx->smem_per_sm - 2 * 1024) / 2;  // 1 KB reserved per CTA
-  // fit in shared memory (keep room for two CTAs per SM when possible)
-  while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm &&
-         (c.S > 512 || c.TG > 32)) {
-    if (c.S > 512) c.S /= 2; else c.TG /= 2;
-  }
-  while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && (c.S > 128 || c.TG > 1)) {
-    if (c.S > 128) c.S /= 2; else c.TG = std::max(1, c.TG / 2);
-  }
-  // enough independent tiles to fill the GPU for small problems
   auto work = [&](int S, int TG) {
     int64_t per = (n / std::max(1, nprob) + S - 1) / S;
     return per * nprob * ((P + TG - 1) / TG);
   };
-  while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && (c.S > 256 || c.TG > 16)) {
-    if (c.S > 256) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
+  if (mode == 0) {
+    // measured on GB300 (n = 1e7, F = 10, depth 4, P = 1024): 16 warps per CTA and
+    // two CTAs per SM beat 8 warps by 1.5x; tiles of 1024 samples with 256 trees
+    // per job were the fastest shape that leaves room for two CTAs
+    c.S = 2048;
+    c.TG = std::min(P, 256);
+    c.warps = 16;
+    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && (c.S > 512 || c.TG > 32)) {
+      if (c.S > 512) c.S /= 2; else c.TG /= 2;
+    }
+    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && (c.S > 128 || c.TG > 1)) {
+      if (c.S > 128) c.S /= 2; else c.TG = std::max(1, c.TG / 2);
+    }
+    // enough independent tiles to fill the GPU for small problems
+    while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && (c.S > 256 || c.TG > 16)) {
+      if (c.S > 256) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
+    }
+    c.warps = std::max(4, std::min(16, c.TG));  // a warp owns a tree
+  } else {
+    // shared-atomic mode: the 16 warps split the chunks of one tree at a time, so
+    // the tile keeps at least 16 chunks and the job's counts ([TG][2^D K]) set TG
+    c.S = 1024;
+    c.warps = 16;
+    c.TG = std::min(P, 256);
+    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && c.TG > 1) c.TG /= 2;
+    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && c.S > 128) c.S /= 2;
+    while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && c.TG > 1) c.TG /= 2;
   }
-  c.warps = std::max(4, std::min(16, c.TG));
   if (ctx->force_S) c.S = ctx->force_S;
   if (ctx->force_TG) c.TG = std::min(ctx->force_TG, std::max(1, P));
   if (ctx->force_warps) c.warps = ctx->force_warps;

@@ -55,6 +55,8 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
 // Choose S / TG / warps for a workload shape (heuristic, tuned by measurement).
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob);
+// 0: ballot counting (2^D K <= 128, D <= 5); 1: shared-memory atomics
+int eval_counting_mode(int D, int K);
 // build the job list for host-side problems (tile counts per problem)
 void eval_build_jobs(const std::vector<int64_t>& counts, const std::vector<int>& pops, int S,
                      int TG, std::vector<EvalJob>* jobs, int64_t* total_tiles);

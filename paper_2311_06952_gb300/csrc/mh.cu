@@ -576,13 +576,17 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   if (!have && !forced) {
     // candidates around the heuristic; each runs the real evaluation of S^1
     std::vector<EvalConfig> cands;
+    const int cmode = eval_counting_mode(Dt, K);
     for (int S : {256, 512, 1024, 2048})
-      for (int TG : {P, std::max(1, P / 2)}) {
+      for (int TG : {cfg.TG, std::max(1, cfg.TG / 2), P}) {
         EvalConfig x = cfg;
         x.S = S;
-        x.TG = TG;
-        x.warps = std::max(4, std::min(16, TG));
-        cands.push_back(x);
+        x.TG = std::min(TG, P);
+        // ballot counting: a warp owns a tree; shared atomics: warps split a tree's chunks
+        x.warps = cmode == 0 ? std::max(4, std::min(16, x.TG)) : 16;
+        bool dup = false;
+        for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG);
+        if (!dup) cands.push_back(x);
       }
     cudaEvent_t e0, e1;
     DEOCT_CUDA_TRY(cudaEventCreate(&e0));
