@@ -153,6 +153,29 @@ def test_eval_launch_shapes_bit_exact(c, shape):
         c.set_eval_config(0, 0, 0, 0)
 
 
+@pytest.mark.parametrize("shape", [(0, 0, 0, 0), (128, 2, 16, 3), (1024, 8, 16, 5), (512, 1, 4, 1)])
+@pytest.mark.parametrize("depth,K", [(7, 3), (4, 29)])
+def test_eval_shared_atomic_mode_shapes_bit_exact(c, shape, depth, K):
+    """Many bins (2^D K > 128): warps split each tree's chunks into shared job counts."""
+    from paper_2311_06952_gb300 import deoct
+    S, TG, warps, grid = shape
+    rng = _rng(400 + depth + K)
+    n, F, P = 17001, 5, 23
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+    try:
+        c.set_eval_config(S, TG, warps, grid)
+        for rb in (2, 4):
+            ds = gpu_dataset(c, X, y, K, rb)
+            counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+            np.testing.assert_array_equal(u32(counts), ref)
+    finally:
+        c.set_eval_config(0, 0, 0, 0)
+
+
 def test_eval_workload1_full_size(c):
     """Population-evaluation workload at its full size: n=1e5, F=20, K=3, 256 depth-3 trees."""
     from paper_2311_06952_gb300 import deoct
