@@ -526,6 +526,7 @@ def main():
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many requests")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--table3", default="", help="comma list of bitcoin-heist,susy,higgs")
+    ap.add_argument("--mh-only", action="store_true", help="only the batched-vs-plain moving-horizon line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -533,6 +534,11 @@ def main():
         return run_serve(args)
     if args.table3:
         return run_table3(args)
+    if args.mh_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"mode": "mh-only", "mh_batched_vs_plain": mh_compare(args)}), flush=True)
+        return 0
     return run_ours(args)
 
 

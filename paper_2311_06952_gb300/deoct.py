@@ -124,11 +124,21 @@ def _check(rc):
         raise DeoctError(rc, msg.decode() if msg else "")
 
 
-def _ptr(t):
+def _ptr(t, itemsize=None):
+    """Address of a host numpy array or a device tensor (checked: CUDA, contiguous,
+    element size as the C ABI expects)."""
     if t is None:
         return None
     if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
         return t.ctypes.data_as(_vp)
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device (got %s)" % t.device)
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if itemsize is not None and t.element_size() != itemsize:
+        raise ValueError("tensor element size %d, expected %d" % (t.element_size(), itemsize))
     return _vp(t.data_ptr())
 
 
@@ -207,8 +217,8 @@ def deoct_encode(ctx: Context, X, rank_bytes: int, ranks_out=None, n_unique_out=
         ranks_out = torch.empty((F, padded_ld(n, rank_bytes)), dtype=dt, device=X.device)
     if n_unique_out is None:
         n_unique_out = torch.empty(F, dtype=torch.int32, device=X.device)
-    _check(load().deoct_encode(ctx.handle, _ptr(X), n, F, rank_bytes, _ptr(ranks_out),
-                               ranks_out.shape[1], _ptr(n_unique_out), _stream(stream)))
+    _check(load().deoct_encode(ctx.handle, _ptr(X, 4), n, F, rank_bytes, _ptr(ranks_out, rank_bytes),
+                               ranks_out.shape[1], _ptr(n_unique_out, 4), _stream(stream)))
     return ranks_out, n_unique_out
 
 
@@ -276,9 +286,9 @@ def deoct_eval_population(ctx: Context, ds: DeviceDataset, a, theta, depth: int,
     if errors_out is None:
         errors_out = torch.empty(P, dtype=torch.int32, device=a.device)
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_eval_population(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx), n_sub,
-                                        _ptr(a), _ptr(theta), P, depth, _ptr(counts_out),
-                                        _ptr(errors_out), _stream(stream)))
+    _check(load().deoct_eval_population(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+                                        _ptr(a, 2), _ptr(theta, 4), P, depth, _ptr(counts_out, 4),
+                                        _ptr(errors_out, 4), _stream(stream)))
     return counts_out, errors_out
 
 
@@ -300,18 +310,18 @@ def deoct_de_init(ctx: Context, ds: DeviceDataset, params: Params, stream_id=0, 
         best = torch.empty(1, dtype=torch.int32, device=dev)
     S = 0 if seeds is None else seeds.shape[0]
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_de_init(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx), n_sub,
-                                ctypes.byref(params), stream_id, _ptr(seeds), S, _ptr(pop),
-                                _ptr(fitness), _ptr(best), _stream(stream)))
+    _check(load().deoct_de_init(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+                                ctypes.byref(params), stream_id, _ptr(seeds, 4), S, _ptr(pop, 4),
+                                _ptr(fitness, 8), _ptr(best, 4), _stream(stream)))
     return pop, fitness, best
 
 
 def deoct_de_step(ctx: Context, ds: DeviceDataset, params: Params, generation: int, pop, fitness,
                   best, stream_id=0, sample_idx=None, stream=None):
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_de_step(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx), n_sub,
-                                ctypes.byref(params), stream_id, generation, _ptr(pop), _ptr(fitness),
-                                _ptr(best), _stream(stream)))
+    _check(load().deoct_de_step(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+                                ctypes.byref(params), stream_id, generation, _ptr(pop, 4), _ptr(fitness, 8),
+                                _ptr(best, 4), _stream(stream)))
     return pop, fitness, best
 
 
