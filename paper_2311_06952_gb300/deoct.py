@@ -195,6 +195,11 @@ class DeviceDataset:
     """A rank-encoded training set resident on the device (tensors kept alive here)."""
 
     def __init__(self, ranks, rank_bytes, n_unique, labels, n, F, K, ld=None):
+        _ptr(ranks, rank_bytes)
+        _ptr(n_unique, 4)
+        _ptr(labels, 1)
+        if ranks.dim() != 2 or ranks.shape[0] != F or ranks.shape[1] < n or labels.numel() < n:
+            raise ValueError("ranks must be [F][ld >= n] and labels [n]")
         self.ranks, self.n_unique, self.labels = ranks, n_unique, labels
         self.rank_bytes, self.n, self.F, self.K = rank_bytes, n, F, K
         self.ld = ranks.shape[1] if ld is None else ld
