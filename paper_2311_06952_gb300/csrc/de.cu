@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
   if (threadIdx.x == 0 && pb.gen) *pb.gen = 1;
 }
 
-__global__ void __launch_bounds__(512) de_step_kernel(const DEArgs a, int g_arg, int flags) {
+__global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags) {
   __shared__ double red_f[32];
   __shared__ int red_i[32];
   __shared__ int best_s;
@@ -166,14 +166,11 @@ __global__ void __launch_bounds__(512) de_step_kernel(const DEArgs a, int g_arg,
   const float ub_a = (float)(pb.F + 1);
   const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
   const float* sb = pb.pop + (int64_t)best * m;
-  // One warp per individual, one lane per gene: every lane computes the Philox
-  // block of its own draw, so the blocks of an individual come in parallel.
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < P; r += nw) {
-    // block 0: r1, r2, q_rand, M (the same value in every lane)
-    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
-    const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
-    const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
+    U64x4 blk = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
+    const uint32_t x0 = draw_from_block(blk, 0), x1 = draw_from_block(blk, 1);
+    const uint32_t x2 = draw_from_block(blk, 2), x3 = draw_from_block(blk, 3);
     int r1 = (int)below(x0, (uint32_t)(P - 1));
     if (r1 >= r) r1 += 1;
     int r2 = (int)below(x1, (uint32_t)(P - 2));
@@ -186,17 +183,17 @@ __global__ void __launch_bounds__(512) de_step_kernel(const DEArgs a, int g_arg,
     const float* s2 = pb.pop + (int64_t)r2 * m;
     const float* sr = pb.pop + (int64_t)r * m;
     float* u = pb.trial + (int64_t)r * m;
-    for (int q = lane; q < m; q += 32) {
+    for (int q = 0; q < m; ++q) {
       const uint32_t s = 4u + (uint32_t)q;
-      const U64x4 blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)(s >> 3), 0ull, a.seed,
-                                      pb.stream_id);
+      if ((s & 7u) == 0u)
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)(s >> 3), 0ull, a.seed,
+                            pb.stream_id);
       const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
       const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
       const float rq = u01(draw_from_block(blk, s));
       u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
     }
-    __syncwarp();
-    for (int t = lane; t < B; t += 32) {
+    for (int t = 0; t < B; ++t) {
       int av;
       uint32_t th;
       decode_gene_pair(u[t], u[B + t], pb.F, pb.n_unique, &av, &th);
@@ -258,8 +255,7 @@ int de_launch_init(deoct_ctx* ctx, const DEArgs& a, cudaStream_t s) {
 int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream_t s) {
   const int nprob = a.probs ? a.nprob : 1;
   if (nprob <= 0) return DEOCT_OK;
-  // 16 warps: the trial phase runs one warp per individual
-  de_step_kernel<<<nprob, 512, 0, s>>>(a, g, flags);
+  de_step_kernel<<<nprob, block_for(a.P), 0, s>>>(a, g, flags);
   count_launch(ctx);
   return check_launch("de_step_kernel");
 }
