@@ -9,8 +9,6 @@
 // So one generation is two launches: evaluator, step(SELECT|TRIAL).  Gene
 // arithmetic is float32 with one rounding per operation (__fsub_rn, __fmul_rn,
 // __fadd_rn); random numbers come from Philox4x64-10 keyed by (seed, stream).
-#include <algorithm>
-
 #include "internal.cuh"
 
 namespace deoct {
@@ -26,7 +24,6 @@ __device__ __forceinline__ const DEProb& prob_of(const DEArgs& a) {
 // V = #{leaf : 0 < n_leaf < n_min}, splits = #{t : a_t >= 1} (ahat_t >= 1).
 __device__ double fitness_of(const uint32_t* __restrict__ c, const float* __restrict__ genes, int B,
                              int L, int K, int64_t n_valid, int n_min, double alpha) {
-  // c: this individual's class counts, leaf-major [L][K]
   int64_t correct = 0;
   uint32_t v = 0;
   for (int l = 0; l < L; ++l) {
@@ -127,54 +124,34 @@ __global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
   if (threadIdx.x == 0 && pb.gen) *pb.gen = 1;
 }
 
-constexpr int kStepSmemWords = 8192;  // staged class counts per chunk of individuals
-
 __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags) {
   __shared__ double red_f[32];
   __shared__ int red_i[32];
   __shared__ int best_s;
   __shared__ int g_s;
-  extern __shared__ uint32_t cnt_sm[];  // [individuals of a chunk][2^D K + pad]
   const DEProb& pb = prob_of(a);
   const int P = a.P, D = a.depth, B = (1 << D) - 1, m = 2 * B, L = 1 << D, K = pb.K;
-  const int LK = L * K;
 
   if (threadIdx.x == 0) g_s = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
 
   if (flags & (DE_FIRST | DE_SELECT)) {
     const bool first = (flags & DE_FIRST) != 0;
-    // Counts reach shared memory with coalesced loads, a chunk of individuals at
-    // a time (odd row stride: one thread per individual reads conflict-free).
-    const int LKp = LK | 1;
-    const bool staged = LKp <= kStepSmemWords;
-    const int CH = staged ? (kStepSmemWords / LKp < P ? kStepSmemWords / LKp : P) : P;
-    for (int c0 = 0; c0 < P; c0 += CH) {
-      const int nc = CH < P - c0 ? CH : P - c0;
-      if (staged) {
-        const uint32_t* src = pb.counts + (int64_t)c0 * LK;
-        for (int e = threadIdx.x; e < nc * LK; e += blockDim.x) {
-          const int i = e / LK;
-          cnt_sm[i * LKp + (e - i * LK)] = src[e];
-        }
-        __syncthreads();
-      }
-      for (int r = c0 + threadIdx.x; r < c0 + nc; r += blockDim.x) {
-        const float* genes = (first ? pb.pop : pb.trial) + (int64_t)r * m;
-        const uint32_t* cr = staged ? cnt_sm + (r - c0) * LKp : pb.counts + (int64_t)r * LK;
-        const double f = fitness_of(cr, genes, B, L, K, pb.n_valid, a.n_min, a.alpha);
-        if (first) {
+    for (int r = threadIdx.x; r < P; r += blockDim.x) {
+      const float* genes = (first ? pb.pop : pb.trial) + (int64_t)r * m;
+      const double f = fitness_of(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
+                                  a.n_min, a.alpha);
+      if (first) {
+        pb.fit[r] = f;
+      } else {
+        pb.fit_trial[r] = f;
+        if (f <= pb.fit[r]) {  // Eq. selection: ties go to the trial
+          float* dst = pb.pop + (int64_t)r * m;
+          for (int q = 0; q < m; ++q) dst[q] = genes[q];
           pb.fit[r] = f;
-        } else {
-          pb.fit_trial[r] = f;
-          if (f <= pb.fit[r]) {  // Eq. selection: ties go to the trial
-            float* dst = pb.pop + (int64_t)r * m;
-            for (int q = 0; q < m; ++q) dst[q] = genes[q];
-            pb.fit[r] = f;
-          }
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
     block_argmin(pb.fit, P, &best_s, red_f, red_i);
     if (threadIdx.x == 0) *pb.best = best_s;
   } else {
@@ -188,12 +165,12 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   const int best = best_s;
   const float ub_a = (float)(pb.F + 1);
   const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
-  const float* __restrict__ sb = pb.pop + (int64_t)best * m;
+  const float* sb = pb.pop + (int64_t)best * m;
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
     // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
-    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
-    const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
-    const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
+    U64x4 blk = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
+    const uint32_t x0 = draw_from_block(blk, 0), x1 = draw_from_block(blk, 1);
+    const uint32_t x2 = draw_from_block(blk, 2), x3 = draw_from_block(blk, 3);
     int r1 = (int)below(x0, (uint32_t)(P - 1));
     if (r1 >= r) r1 += 1;
     int r2 = (int)below(x1, (uint32_t)(P - 2));
@@ -202,26 +179,19 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
     if (r2 >= hi) r2 += 1;
     const int qrand = (int)below(x2, (uint32_t)m);
     const float M = a.dither ? u01(x3) : a.M;
-    const float* __restrict__ s1 = pb.pop + (int64_t)r1 * m;
-    const float* __restrict__ s2 = pb.pop + (int64_t)r2 * m;
-    const float* __restrict__ sr = pb.pop + (int64_t)r * m;
-    float* __restrict__ u = pb.trial + (int64_t)r * m;
-    // genes in groups of one Philox block (draw s = q + 4 lives in block s / 8):
-    // the group's loads are independent of each other and of the block
-    for (int k = 0; 8 * k - 4 < m; ++k) {
-      const U64x4 blk = k == 0 ? blk0
-                               : philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)k, 0ull, a.seed,
-                                               pb.stream_id);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int q = 8 * k + e - 4;
-        if (q >= 0 && q < m) {
-          const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
-          const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
-          const float rq = u01(draw_from_block(blk, (uint32_t)(8 * k + e)));
-          u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
-        }
-      }
+    const float* s1 = pb.pop + (int64_t)r1 * m;
+    const float* s2 = pb.pop + (int64_t)r2 * m;
+    const float* sr = pb.pop + (int64_t)r * m;
+    float* u = pb.trial + (int64_t)r * m;
+    for (int q = 0; q < m; ++q) {
+      const uint32_t s = 4u + (uint32_t)q;
+      if ((s & 7u) == 0u)
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)(s >> 3), 0ull, a.seed,
+                            pb.stream_id);
+      const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
+      const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
+      const float rq = u01(draw_from_block(blk, s));
+      u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
     }
     for (int t = 0; t < B; ++t) {
       int av;
@@ -285,7 +255,7 @@ int de_launch_init(deoct_ctx* ctx, const DEArgs& a, cudaStream_t s) {
 int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream_t s) {
   const int nprob = a.probs ? a.nprob : 1;
   if (nprob <= 0) return DEOCT_OK;
-  de_step_kernel<<<nprob, block_for(a.P), kStepSmemWords * 4, s>>>(a, g, flags);
+  de_step_kernel<<<nprob, block_for(a.P), 0, s>>>(a, g, flags);
   count_launch(ctx);
   return check_launch("de_step_kernel");
 }
