@@ -306,7 +306,6 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     if (P.tma) {
       if (!staged && threadIdx.x == 0) issue_tile_tma(P, s0, ns, S, W, stageb, &mbar);
     } else {
-      RT* dst = reinterpret_cast<RT*>(tileb);
       const RT* src = static_cast<const RT*>(P.ranks);
       for (int e = threadIdx.x; e < P.F * S; e += blockDim.x) {
         int f = e / S, j = e - f * S;
@@ -320,7 +319,6 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
               src[(int64_t)f * P.ld + col];
         }
       }
-      (void)dst;
     }
     staged = false;
     // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
@@ -570,7 +568,7 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
                               int nprob) {
   EvalConfig c;
   const int mode = eval_mode(D, K);
-  const int limit = std::min(ctx->max_smem_optin, 227 * 1024);
+  const int limit = std::min(ctx->max_smem_optin, 227 * 1024) - 1024;  // room for static smem
   const size_t two_per_sm = (size_t)(ctx->smem_per_sm - 2 * 1024) / 2;  // 1 KB reserved per CTA
   auto work = [&](int S, int TG) {
     int64_t per = (n / std::max(1, nprob) + S - 1) / S;

@@ -168,3 +168,22 @@ def test_moving_horizon_deoct_seeds_bit_exact(c, name, both):
     for k in ("kind", "theta", "node_fit", "leaf_class"):
         np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
     np.testing.assert_array_equal(out["a"].astype(np.int32), ref["a"])
+
+
+@pytest.mark.parametrize("depth,horizon,F,n_min", [(1, 2, 3, 1), (3, 5, 1, 1), (4, 2, 2, 0)])
+def test_moving_horizon_edge_shapes(c, depth, horizon, F, n_min):
+    """Depth 1 (a single depth-1 search), horizon beyond the depth, one feature, n_min = 0."""
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(600 + depth * 10 + F)
+    X = np.round(rng.random((2000, F)), 2).astype(np.float32)
+    y = rng.integers(0, 3, 2000).astype(np.uint8)
+    ds = gpu_dataset(c, X, y, 3, 2)
+    ranks, nu = oracle.encode(X)
+    ref = oracle.mh(ranks, nu, y, 3, depth=depth, horizon=horizon, P=16, G=5, seed=1, n_min=n_min)
+    for flags in (0, deoct.DEOCT_BATCHED):
+        out = deoct.deoct_fit_moving_horizon(c, ds, deoct.make_params(depth, 16, 5, seed=1, horizon=horizon,
+                                                                      n_min=n_min, flags=flags))
+        np.testing.assert_array_equal(out["a"].astype(np.int32), ref["a"])
+        np.testing.assert_array_equal(out["theta"], ref["theta"])
+        np.testing.assert_array_equal(out["kind"], ref["kind"])
+        np.testing.assert_array_equal(out["leaf_class"], ref["leaf_class"])

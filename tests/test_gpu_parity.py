@@ -335,3 +335,24 @@ def test_invalid_arguments_are_rejected(c):
         deoct.deoct_fit_subtree(c, ds, deoct.make_params(2, 16, 1))
     # and the context recovers
     deoct.deoct_fit_subtree(c, ds, deoct.make_params(2, 16, 1))
+
+
+@pytest.mark.parametrize("rb,extra", [(4, 3), (2, 5), (4, 0)])
+def test_eval_with_unaligned_row_stride(c, rb, extra):
+    """A caller-chosen row stride that breaks 16-byte alignment takes the plain-load path."""
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(500 + rb + extra)
+    n, F, K, depth, P = 3001, 4, 3, 3, 30
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ld = n + extra
+    dt = torch.int16 if rb == 2 else torch.int32
+    ranks = torch.zeros((F, ld), dtype=dt, device="cuda")
+    nu = torch.empty(F, dtype=torch.int32, device="cuda")
+    deoct.deoct_encode(c, to_dev(X), rb, ranks_out=ranks, n_unique_out=nu)
+    ds = deoct.DeviceDataset(ranks, rb, nu, to_dev(y), n, F, K)
+    r_ref, nu_ref = oracle.encode(X)
+    a, th = datagen.random_population(nu_ref, P, depth, rng, allow_nosplit=True)
+    counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+    np.testing.assert_array_equal(u32(counts), oracle.eval_counts(r_ref, y, K, a, th, depth))
