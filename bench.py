@@ -344,8 +344,49 @@ def eval_workload1(args):
     ms = float(np.median(times))
     evals = w["P"] * w["X"].shape[0]
     return {"workload": "eval-gmm: n=1e5, F=20 Gaussian mixture, K=3, 256 random depth-3 trees, "
-                        "uint32 ranks, one evaluation (pack + evaluate + errors), L2 flushed",
-            "ms": ms, "evals": evals, "evals_per_s": evals / (ms / 1000.0), "samples": len(times)}
+                        "uint32 ranks, one evaluation (one launch: pack + evaluate + errors), L2 flushed",
+            "ms": ms, "evals": evals, "evals_per_s": evals / (ms / 1000.0), "samples": len(times),
+            "launches_per_eval": 1}
+
+
+def eval_p_sweep(ctx, ranks, nu, yd, n, F, K, peaks, depth=4):
+    """Where the population evaluator turns HBM-bound: one evaluation of P random depth-4
+    trees on the main workload's resident ranks (n = 1e7, uint16, 200 MB: larger than L2) for
+    P from 1 to 1024, timed on the evaluator launch.  Algorithmic bytes n (F w + 1) are read
+    once per tree group whatever P is, so below the crossover P* = R_alu t_hbm / n (R_alu =
+    the compute-bound evals/s, t_hbm = bytes / measured copy bandwidth) HBM bounds the launch."""
+    import torch
+    from paper_2311_06952_gb300 import datagen, deoct
+    ds = deoct.DeviceDataset(ranks, 2, nu, yd, n, F, K)
+    nu_h = nu.cpu().numpy().view(np.uint32)
+    alg = n * (F * 2 + 1)
+    rows = []
+    for P in (1, 2, 4, 8, 16, 64, 256, 1024):
+        a, th = datagen.random_population(nu_h, P, depth, np.random.Generator(np.random.PCG64(50 + P)))
+        ad = torch.from_numpy(a.astype(np.int16)).cuda()
+        td = torch.from_numpy(th.view(np.int32)).cuda()
+        counts = torch.empty((P, 1 << depth, K), dtype=torch.int32, device="cuda")
+        errs = torch.empty(P, dtype=torch.int32, device="cuda")
+        ms = []
+        for it in range(8):
+            ctx.reset_stats()
+            ctx.set_timing(True)
+            deoct.deoct_eval_population(ctx, ds, ad, td, depth, counts_out=counts, errors_out=errs)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            ctx.set_timing(False)
+            if it >= 3:
+                ms.append(st["eval_ms"] / max(1, st["eval_timed"]))
+        m = float(np.median(ms))
+        gbs = alg / (m / 1000.0) / 1e9
+        rows.append({"P": P, "launch_ms": m, "evals_per_s": P * n / (m / 1000.0), "alg_gbs": gbs,
+                     "hbm_frac": gbs / peaks["hbm_gbs"]})
+    t_hbm = alg / (peaks["hbm_gbs"] * 1e9)
+    r_alu = rows[-1]["evals_per_s"]
+    return {"workload": "large-deoct ranks (n=1e7, F=10, uint16, K=2), P random depth-4 trees, "
+                        "one evaluation launch each (fused pack + evaluate + errors)",
+            "algorithmic_bytes": alg, "t_hbm_us": t_hbm * 1e6, "crossover_P": r_alu * t_hbm / n,
+            "rows": rows}
 
 
 PAPER_TABLE3_S = {  # MH-DEOCT training time on an A100 (Table 3), seconds, D = 2 / 4 / 8
@@ -498,6 +539,7 @@ def run_ours(args):
         "result": {"fitness": res[2], "train_accuracy": 1.0 - res[2] / n},
     }
     if world == 1 and not args.no_mh:
+        line["p_sweep"] = eval_p_sweep(ctx, ranks, nu, yd, n, F, K, peaks)
         line["population_eval"] = eval_workload1(args)
         line["mh_batched_vs_plain"] = mh_compare(args)
     if world == 1 and not args.no_cpu_baseline:

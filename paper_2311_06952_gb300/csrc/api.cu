@@ -129,6 +129,7 @@ static EvalProb single_prob(const deoct_dataset* ds, const int32_t* idx, int64_t
   const bool aligned = (reinterpret_cast<uintptr_t>(ds->ranks) % 16 == 0) &&
                        ((ds->ld * ds->rank_bytes) % 16 == 0);
   p.tma = (idx == nullptr && aligned) ? 1 : 0;
+  p.lab_tma = (p.tma && reinterpret_cast<uintptr_t>(ds->labels) % 16 == 0) ? 1 : 0;
   return p;
 }
 
@@ -145,6 +146,36 @@ static int eval_single(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* i
   plan.Kmax = ds->K;
   plan.Pmax = P;
   plan.max_count = n_sub;
+  return eval_launch(ctx, ds->rank_bytes, depth, plan, cfg, s);
+}
+
+// One evaluation of caller-given trees in a single launch: the evaluator packs
+// the trees while building its node tables and its last CTA writes errors and
+// counts (see EvalPlan::ticket).  The accumulator slot is zero at rest: it is
+// zeroed when (re)allocated and by every launch that used it.
+static int eval_single_fused(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* idx,
+                             int64_t n_sub, const uint16_t* a, const uint32_t* theta, int P,
+                             int depth, uint32_t* counts_out, uint32_t* errors_out,
+                             cudaStream_t s) {
+  const size_t L = (size_t)1 << depth;
+  const size_t bytes = 16 + sizeof(uint32_t) * (size_t)P * L * ds->K;
+  const bool grows = ctx->scratch[SL_EVAL_ACC].bytes < bytes;
+  uint32_t* base = nullptr;
+  DEOCT_TRY(scratch_get(ctx, SL_EVAL_ACC, bytes, (void**)&base));
+  if (grows) DEOCT_CUDA_TRY(cudaMemsetAsync(base, 0, ctx->scratch[SL_EVAL_ACC].bytes, s));
+  EvalConfig cfg = eval_choose_config(ctx, ds->rank_bytes, depth, ds->F, ds->K, P, n_sub, 1);
+  EvalPlan plan;
+  plan.single = single_prob(ds, idx, n_sub, nullptr, base + 4, P);
+  plan.single.a16 = a;
+  plan.single.th32 = theta;
+  plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
+  plan.Fmax = ds->F;
+  plan.Kmax = ds->K;
+  plan.Pmax = P;
+  plan.max_count = n_sub;
+  plan.ticket = base;
+  plan.counts_out = counts_out;
+  plan.errors_out = errors_out;
   return eval_launch(ctx, ds->rank_bytes, depth, plan, cfg, s);
 }
 
@@ -474,6 +505,9 @@ int deoct_eval_population(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t
   if (P < 1 || P > kMaxPop * 64) return set_error(DEOCT_ERR_INVALID, "P = %d out of range", P);
   if (depth < 1 || depth > kMaxDepth) return set_error(DEOCT_ERR_INVALID, "depth out of range");
   const int B = (1 << depth) - 1, L = 1 << depth;
+  if (n_sub > 0)
+    return eval_single_fused(ctx, ds, sample_idx, n_sub, a, theta, P, depth, counts_out, errors_out, s);
+  // empty set: the trees are still validated; counts and errors are zero
   uint32_t* nodes = nullptr;
   DEOCT_TRY(scratch_get(ctx, SL_PACKED, sizeof(uint32_t) * (size_t)P * B, (void**)&nodes));
   uint32_t* counts = counts_out;

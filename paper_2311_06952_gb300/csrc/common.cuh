@@ -69,6 +69,7 @@ enum ScratchSlot : int {
   SL_MH_D1KEYS, SL_MH_D1VALS, SL_MH_D1K1, SL_MH_D1V1, SL_MH_D1BEST, SL_MH_POP, SL_MH_FIT,
   SL_MH_BEST, SL_MH_HOSTBUF, SL_D1_RESULT, SL_MISC,
   SL_MH_RANKS2, SL_MH_LABELS2, SL_MH_IDX2, SL_MH_POS2, SL_MH_SUB, SL_MH_SUBHIST, SL_MH_SEEDS,
+  SL_EVAL_ACC,  // zero at rest: ticket word, then the counts of one fused evaluation
   SL_COUNT
 };
 
@@ -145,6 +146,9 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),

@@ -1,223 +1,23 @@
-// eval.cu -- population fitness evaluation (Algorithm 1, Section 3.2).
+// eval.cu -- population fitness evaluation (Algorithm 1, Section 3.2): the
+// re-laid kernel, the launch decision between it and the streaming kernel
+// (eval_stream.cu), and the evaluator's small host-side helpers.
 //
-// Layout of the work: persistent CTAs split a flattened sequence of tiles
-// (jobs x tiles; a job is one tree group of one subproblem) into equal
-// contiguous ranges.  Per tile a CTA stages the feature-major rank rows of S
-// samples in shared memory (1-D TMA bulk copies when the rows are aligned,
-// plain loads for gathered subsets), so each sample is read from HBM once per
-// tree group, and routes every sample through every tree of the job, whose
-// nodes sit in shared memory.  Counting:
-//  - ballot mode (2^D * K <= 128): the routing predicate of level d is a warp
-//    ballot B_d over 32 samples; lane b owns bin b = leaf*K + k and adds
-//    popc(Y_k & AND_d (B_d or ~B_d by bit d of leaf)) -- the class masks Y_k
-//    are precomputed per tile, so counting costs no atomics;
-//  - atomic mode (larger 2^D * K): per-warp shared histogram with atomics.
-// Counts of a job accumulate in shared memory and reach HBM with one atomic
-// add per (tree, bin) per CTA.
-#include <algorithm>
-
-#include "internal.cuh"
+// The re-laid kernel stages each tile through one landing zone per CTA and,
+// for uint16 ranks, re-lays the rows into a chunk-pair-interleaved compute
+// tile so that 16 warps routing 16+ trees read shared memory without bank
+// conflicts; the next tile's bulk copies fly while the current one is routed.
+// It also holds the shared-atomic counting mode for 2^D K > 128 bins: all
+// warps split each tree's chunks and add into the job's shared counts.
+#include "eval_kernel.cuh"
 
 namespace deoct {
 
+using namespace evk;
+
 namespace {
 
-template <int W>
-struct RankT;
-template <>
-struct RankT<2> {
-  typedef uint16_t T;
-};
-template <>
-struct RankT<4> {
-  typedef uint32_t T;
-};
-
-constexpr int kQMax = 4;  // ballot mode: up to 4 bins per lane (2^D * K <= 128)
-
-struct EvalArgs {
-  EvalProb single;
-  const EvalProb* probs;
-  const EvalJob* jobs;
-  int njobs;
-  int single_ntiles;  // tiles per job when `probs` is null
-  int64_t total_tiles;
-  int S, TG, Fmax, Kmax;
-  int* status;
-};
-
-struct JobView {
-  const EvalProb* p;
-  int64_t tile;  // tile index within the job
-  int32_t job, tree0, ntrees;
-};
-
-__device__ __forceinline__ void lookup_job(const EvalArgs& a, int64_t gt, JobView* v) {
-  if (a.probs == nullptr) {
-    int64_t job = gt / a.single_ntiles;
-    v->p = &a.single;
-    v->job = (int32_t)job;
-    v->tile = gt - job * a.single_ntiles;
-    v->tree0 = (int32_t)job * a.TG;
-    int rem = a.single.P - v->tree0;
-    v->ntrees = rem < a.TG ? rem : a.TG;
-    return;
-  }
-  int lo = 0, hi = a.njobs - 1;  // last job with tile_begin <= gt
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (a.jobs[mid].tile_begin <= gt) lo = mid; else hi = mid - 1;
-  }
-  const EvalJob& j = a.jobs[lo];
-  v->p = a.probs + j.prob;
-  v->job = lo;
-  v->tile = gt - j.tile_begin;
-  v->tree0 = j.tree0;
-  v->ntrees = j.ntrees;
-}
-
-__host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
-
-// Shared-memory layout, shared by host sizing and the kernel:
-//   tile    [F][S] ranks in the compute layout (see tile_offset)
-//   stage   [F][S] TMA landing zone (uint16 only; the uint32 path lands in `tile`)
-//   nodes   [TG][B] {shared address of the feature row, theta}
-//   aux     ballot mode: class masks [S/32][Q][32]; atomic mode: labels [S]
-//   cnt     job counts [TG][2^D K] (both modes)
-struct SmemLayout {
-  size_t tile, stage, nodes, aux, cnt, total;
-};
-__host__ __device__ __forceinline__ SmemLayout smem_layout(int mode, int W, int D, int S, int TG,
-                                                           int Fmax, int Kmax, int warps) {
-  const int B = (1 << D) - 1, L = 1 << D;
-  const int LK = L * Kmax;
-  const size_t rows = align128((size_t)Fmax * S * W);
-  SmemLayout s;
-  s.tile = 0;
-  s.stage = rows;
-  s.nodes = s.stage + (W == 2 ? rows : 0);
-  s.aux = s.nodes + align128((size_t)TG * B * 8);
-  if (mode == 0) {
-    const int Q = (LK + 31) / 32;
-    s.cnt = s.aux + align128((size_t)S * Q * 4);
-    s.total = s.cnt + align128((size_t)TG * LK * 4);
-  } else {
-    s.cnt = s.aux + align128((size_t)S);
-    s.total = s.cnt + align128((size_t)TG * LK * 4);
-  }
-  return s;
-}
-
-// Byte offset of sample j inside a feature row of the compute tile.  uint32
-// ranks: natural order (lane l of a warp reads bank l).  uint16 ranks: the two
-// chunks of 32 samples of a chunk pair share 32-bit words -- word l of pair p
-// holds sample 64p+l (low half) and 64p+32+l (high half) -- so a warp reading
-// one chunk touches 32 distinct banks whatever rows its lanes are on.
-template <int W>
-__device__ __forceinline__ uint32_t tile_offset(uint32_t j) {
-  if (W == 4) return j * 4u;
-  return (j >> 6) * 128u + (j & 31u) * 4u + ((j >> 5) & 1u) * 2u;
-}
-// offset between the two chunks of a pair for the same lane
-template <int W>
-struct PairGeom {
-  static constexpr uint32_t kSecond = (W == 2) ? 2u : 128u;
-  static constexpr uint32_t kPairStride = 64u * W;
-};
-
-template <int W>
-__device__ __forceinline__ uint32_t lds_rank(uint32_t addr) {
-  uint32_t v;
-  if (W == 2) {
-    unsigned short h;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(addr));
-    v = h;
-  } else {
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  }
-  return v;
-}
-__device__ __forceinline__ uint2 lds_node(uint32_t addr) {
-  uint2 v;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
-  return v;
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
-
-// Route 64 samples (the two chunks of pair p) of one tree and add the bin
-// counts owned by this lane.  Ballot of level d = "went right" at depth d for
-// the 32 samples of a chunk; bin b = leaf*K + k is owned by lane b % 32.
-template <int W, int D, int Q>
-__device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
-                                           uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
-                                           uint32_t tnb48, uint32_t ntnb, uint32_t ymA, uint32_t ymB,
-                                           const uint32_t (&cst)[Q][D], uint32_t (&cnt)[Q]) {
-  constexpr uint32_t SEC = PairGeom<W>::kSecond;
-  uint32_t BA[D], BB[D];
-  // level 0: the root is the same node for every lane
-  const uint32_t ra0 = lds_rank<W>(row0 + jb);
-  const uint32_t rb0 = lds_rank<W>(row0 + jb + SEC);
-  const bool pa0 = ra0 >= th0, pb0 = rb0 >= th0;
-  BA[0] = __ballot_sync(0xFFFFFFFFu, pa0);
-  BB[0] = __ballot_sync(0xFFFFFFFFu, pb0);
-  if (D >= 2) {
-    // level 1: two candidate nodes held in registers
-    const uint32_t rowa = pa0 ? row3 : row2, tha = pa0 ? th3 : th2;
-    const uint32_t rowb = pb0 ? row3 : row2, thb = pb0 ? th3 : th2;
-    const uint32_t ra1 = lds_rank<W>(rowa + jb);
-    const uint32_t rb1 = lds_rank<W>(rowb + jb + SEC);
-    const bool pa1 = ra1 >= tha, pb1 = rb1 >= thb;
-    BA[1 < D ? 1 : 0] = __ballot_sync(0xFFFFFFFFu, pa1);
-    BB[1 < D ? 1 : 0] = __ballot_sync(0xFFFFFFFFu, pb1);
-    // shared address of node t = 4 + 2 p0 + p1
-    uint32_t aa = (pa0 ? tnb48 : tnb32) + (pa1 ? 8u : 0u);
-    uint32_t ab = (pb0 ? tnb48 : tnb32) + (pb1 ? 8u : 0u);
-#pragma unroll
-    for (int d = 2; d < D; ++d) {
-      const uint2 na = lds_node(aa);
-      const uint2 nb = lds_node(ab);
-      const uint32_t ra = lds_rank<W>(na.x + jb);
-      const uint32_t rb = lds_rank<W>(nb.x + jb + SEC);
-      const bool pa = ra >= na.y, pb = rb >= nb.y;
-      BA[d] = __ballot_sync(0xFFFFFFFFu, pa);
-      BB[d] = __ballot_sync(0xFFFFFFFFu, pb);
-      if (d + 1 < D) {  // node 2t + p: address 2 addr(t) - base + 8 p
-        aa = 2u * aa + ntnb + (pa ? 8u : 0u);
-        ab = 2u * ab + ntnb + (pb ? 8u : 0u);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    uint32_t ma = lds_u32(ymA + q * 128u);
-    uint32_t mb = lds_u32(ymB + q * 128u);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      ma &= BA[d] ^ cst[q][d];
-      mb &= BB[d] ^ cst[q][d];
-    }
-    cnt[q] += __popc(ma) + __popc(mb);
-  }
-}
-
-// Stage the rank rows of one tile.  TMA path: one elected thread issues a 1-D
-// bulk copy per feature row into `dst` and arms the mbarrier.
-__device__ __forceinline__ void issue_tile_tma(const EvalProb& P, int64_t s0, int ns, int S, int W,
-                                               unsigned char* dst, uint64_t* bar) {
-  fence_proxy_async_smem();
-  const uint32_t bytes = ((uint32_t)ns * W + 15u) & ~15u;
-  mbar_arrive_expect_tx(bar, bytes * (uint32_t)P.F);
-  const unsigned char* src = static_cast<const unsigned char*>(P.ranks);
-  for (int f = 0; f < P.F; ++f)
-    bulk_g2s(dst + (size_t)f * S * W, src + ((int64_t)f * P.ld + s0) * W, bytes, bar);
-}
-
 template <int W, int D, int MODE, int Q>
-__global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(512, 2) eval_kernel(const EvalArgs a) {
   constexpr int B = (1 << D) - 1;
   constexpr int L = 1 << D;
   typedef typename RankT<W>::T RT;
@@ -228,12 +28,13 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  const SmemLayout lay = smem_layout(MODE, W, D, S, a.TG, a.Fmax, a.Kmax, nw);
+  const SmemLayout lay = smem_layout(MODE, W, D, S, a.TG, a.Fmax, a.Kmax, nw, a.lab_stage);
   unsigned char* tileb = smem + lay.tile;
   unsigned char* stageb = (W == 2) ? smem + lay.stage : tileb;
   uint2* nodes_s = reinterpret_cast<uint2*>(smem + lay.nodes);
   uint32_t* aux32 = reinterpret_cast<uint32_t*>(smem + lay.aux);
   uint8_t* lab_s = smem + lay.aux;
+  unsigned char* lab_land = smem + lay.lab;
   uint32_t* cnt_s = reinterpret_cast<uint32_t*>(smem + lay.cnt);
   const uint32_t tile_sa = smem_u32(tileb);
   const uint32_t nodes_sa = smem_u32(nodes_s);
@@ -242,7 +43,6 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   const int64_t T = a.total_tiles;
   const int64_t t0 = (int64_t)blockIdx.x * T / gridDim.x;
   const int64_t t1 = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
-  if (t0 >= t1) return;
 
   if (threadIdx.x == 0) {
     mbar_init(&mbar, 1);
@@ -257,42 +57,21 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
   uint32_t cst[Q][D];  // ballot mode: per owned bin, "right" (0) or "left" (~0) at level d
   bool staged = false; // the current tile's rows are already in flight (prefetched)
 
-  auto flush = [&](const JobView& v) {
-    uint32_t* dst = v.p->counts + (int64_t)v.tree0 * LK;
-    for (int e = threadIdx.x; e < v.ntrees * LK; e += blockDim.x) {
-      uint32_t c = cnt_s[e];
-      if (c) atomicAdd(dst + e, c);
-    }
-  };
-
   for (int64_t gt = t0; gt < t1; ++gt) {
-    JobView nv;
-    lookup_job(a, gt, &nv);
+    JobView nv;  // job and tile of gt: a search at the first tile, then a step
+    if (gt == t0) {
+      lookup_job(a, gt, &nv);
+    } else {
+      nv = jv;
+      advance_job(a, gt, &nv);
+    }
     if (nv.job != cur_job) {
-      if (cur_job >= 0) flush(jv);
+      if (cur_job >= 0) flush_job(jv, cnt_s, LK, blockDim.x);
       __syncthreads();
       jv = nv;
       cur_job = nv.job;
-      K = jv.p->K;
-      LK = L * K;
-      // nodes -> {shared address of the feature row in the tile, theta}
-      const uint32_t* gn = jv.p->nodes + (int64_t)jv.tree0 * B;
-      for (int e = threadIdx.x; e < jv.ntrees * B; e += blockDim.x) {
-        uint32_t pk = gn[e];
-        uint32_t f = pk >> 24;
-        nodes_s[e] = make_uint2(tile_sa + f * (uint32_t)S * (uint32_t)W, pk & kThetaMask);
-      }
-      for (int e = threadIdx.x; e < jv.ntrees * LK; e += blockDim.x) cnt_s[e] = 0;
-      if (MODE == 0) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          int b = lane + 32 * q;
-          int leaf = (b < LK) ? b / K : 0;
-#pragma unroll
-          for (int d = 0; d < D; ++d)
-            cst[q][d] = ((leaf >> (D - 1 - d)) & 1) ? 0u : 0xFFFFFFFFu;
-        }
-      }
+      setup_job<D, Q, MODE == 0>(jv, nodes_s, cnt_s, tile_sa, S, W, a.status, lane, blockDim.x, cst,
+                                 &K, &LK);
     }
     jv.tile = nv.tile;  // the tile changes every iteration, the job only sometimes
     const EvalProb& P = *jv.p;
@@ -302,9 +81,10 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     const int nch = (ns + 31) >> 5;
     const int npair = (nch + 1) >> 1;
 
-    // ---- stage rank rows -------------------------------------------------
+    // ---- stage rank rows (and labels) ------------------------------------
     if (P.tma) {
-      if (!staged && threadIdx.x == 0) issue_tile_tma(P, s0, ns, S, W, stageb, &mbar);
+      if (!staged && warp == 0)
+        issue_tile_tma(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane);
     } else {
       const RT* src = static_cast<const RT*>(P.ranks);
       for (int e = threadIdx.x; e < P.F * S; e += blockDim.x) {
@@ -321,110 +101,79 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
       }
     }
     staged = false;
-    // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
-    if (MODE == 0) {
-      for (int c = warp; c < 2 * npair; c += nw) {
-        int j = c * 32 + lane;
-        uint32_t y = 0xFFu;
-        if (j < ns) {
-          int64_t col = P.idx ? (int64_t)P.idx[s0 + j] : s0 + j;
-          if ((uint64_t)col >= (uint64_t)P.ncols) col = 0;
-          y = P.labels[col];
-        }
-        uint32_t mine[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) mine[q] = 0u;
-        for (int k = 0; k < K; ++k) {
-          uint32_t m = __ballot_sync(0xFFFFFFFFu, y == (uint32_t)k);
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            int b = lane + 32 * q;
-            if (b < LK && (b % K) == k) mine[q] = m;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
-      }
-    } else {
-      for (int j = threadIdx.x; j < 2 * npair * 32; j += blockDim.x) {
-        uint8_t y = 0xFF;
-        if (j < ns) {
-          int64_t col = P.idx ? (int64_t)P.idx[s0 + j] : s0 + j;
-          if ((uint64_t)col >= (uint64_t)P.ncols) col = 0;
-          y = P.labels[col];
-        }
-        lab_s[j] = y;
-      }
-    }
     if (P.tma) {
-      int ok = mbar_wait_bounded(&mbar, phase, a.status) ? 1 : 0;
-      phase ^= 1u;
+      // one thread polls the mbarrier while the others sleep in the CTA
+      // barrier; each then acquires the landed bytes through the completed
+      // phase (the test succeeds at once)
+      int ok = 1;
+      if (threadIdx.x == 0) ok = mbar_wait_bounded(&mbar, phase, a.status) ? 1 : 0;
       if (__syncthreads_or(!ok)) {
         // timed out (status recorded): give the copies in flight one more
         // bounded wait before the CTA leaves
-        if (threadIdx.x == 0) mbar_wait_bounded(&mbar, phase ^ 1u, a.status);
+        if (threadIdx.x == 0) mbar_wait_bounded(&mbar, phase, a.status);
         __syncthreads();
-        return;
+        break;  // the CTA still takes its ticket below
       }
+      if (threadIdx.x != 0) mbar_try_wait(&mbar, phase);
+      phase ^= 1u;
       if (W == 2) {
-        // stage (natural order) -> tile (chunk-pair interleaved)
-        const uint16_t* st = reinterpret_cast<const uint16_t*>(stageb);
-        uint32_t* tw = reinterpret_cast<uint32_t*>(tileb);
-        const int words = npair * 32;  // per row
-        for (int e = threadIdx.x; e < P.F * words; e += blockDim.x) {
-          int f = e / words, w = e - f * words;
-          int pp = w >> 5, l = w & 31;
-          const uint16_t* srow = st + (size_t)f * S + pp * 64 + l;
-          tw[(size_t)f * (S / 2) + w] = (uint32_t)srow[0] | ((uint32_t)srow[32] << 16);
-        }
-        __syncthreads();
-        // prefetch the next tile of this CTA into the free landing zone
-        if (gt + 1 < t1) {
-          JobView xv;
-          lookup_job(a, gt + 1, &xv);
-          const EvalProb& X = *xv.p;
-          if (X.tma) {
-            if (threadIdx.x == 0) {
-              const int64_t xs0 = X.start + xv.tile * (int64_t)S;
-              const int64_t xrem = X.start + X.count - xs0;
-              issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, &mbar);
-            }
-            staged = true;
+        // stage (natural order) -> tile (chunk-pair interleaved): a task is
+        // four tile words of one row, from two 8-byte loads (samples 64p+4m..
+        // +3 and 64p+32+4m..+3) and four byte permutes, one 16-byte store
+        const int quads = npair * 8;  // tasks per row
+        const int tasks = P.F * quads;
+        const int fstep = blockDim.x / quads, qstep = blockDim.x - fstep * quads;
+        int f = threadIdx.x / quads, q = threadIdx.x - f * quads;
+        for (int e = threadIdx.x; e < tasks; e += blockDim.x) {
+          const int pp = q >> 3, m = q & 7;
+          const unsigned char* srow = stageb + (size_t)f * S * 2 + pp * 128 + m * 8;
+          const uint2 lo = *reinterpret_cast<const uint2*>(srow);
+          const uint2 hi = *reinterpret_cast<const uint2*>(srow + 64);
+          uint4 o;
+          o.x = __byte_perm(lo.x, hi.x, 0x5410);
+          o.y = __byte_perm(lo.x, hi.x, 0x7632);
+          o.z = __byte_perm(lo.y, hi.y, 0x5410);
+          o.w = __byte_perm(lo.y, hi.y, 0x7632);
+          *reinterpret_cast<uint4*>(tileb + (size_t)f * S * 2 + pp * 128 + m * 16) = o;
+          q += qstep;
+          f += fstep;
+          if (q >= quads) {
+            q -= quads;
+            ++f;
           }
         }
       }
+    }
+    // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
+    const int lab_done = tma_label_bytes(P, ns, a.lab_stage);
+    if (MODE == 0) {
+      class_masks<Q>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, nw, aux32);
     } else {
-      __syncthreads();
+      for (int j = threadIdx.x; j < 2 * npair * 32; j += blockDim.x)
+        lab_s[j] = (uint8_t)tile_label(P, lab_land, lab_done, s0, j, ns);
+    }
+    __syncthreads();
+    // prefetch the next tile of this CTA into the free landing zones (the
+    // uint16 path routes from the re-laid tile, so its landing zone is free)
+    if (W == 2 && P.tma && gt + 1 < t1) {
+      JobView xv = jv;
+      advance_job(a, gt + 1, &xv);
+      const EvalProb& X = *xv.p;
+      if (X.tma) {
+        if (warp == 0) {
+          const int64_t xs0 = X.start + xv.tile * (int64_t)S;
+          const int64_t xrem = X.start + X.count - xs0;
+          issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, lab_land,
+                         a.lab_stage, &mbar, lane);
+        }
+        staged = true;
+      }
     }
 
     // ---- route + count ---------------------------------------------------
     if (MODE == 0) {
-      // ballot mode: a warp owns a tree and walks all chunk pairs of the tile
-      for (int i = warp; i < jv.ntrees; i += nw) {
-        const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
-        const uint2 n1 = nodes_s[i * B];
-        uint2 n2 = n1, n3 = n1;
-        if (D >= 2) {
-          n2 = nodes_s[i * B + 1];
-          n3 = nodes_s[i * B + 2];
-        }
-        uint32_t cnt[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) cnt[q] = 0u;
-        const uint32_t ntnb = 0u - tnb;
-        for (int pp = 0; pp < npair; ++pp) {
-          const uint32_t jb = (uint32_t)pp * PairGeom<W>::kPairStride + (uint32_t)lane * 4u;
-          const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
-          const uint32_t ymB = ymA + Q * 128u;
-          route_pair<W, D, Q>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u, tnb + 48u, ntnb,
-                              ymA, ymB, cst, cnt);
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          int b = lane + 32 * q;
-          if (b < LK) cnt_s[i * LK + b] += cnt[q];
-        }
-      }
+      route_group<W, D, Q, false>(jv.ntrees, npair, 0u, nodes_s, nodes_sa, aux_sa, cst, cnt_s, LK,
+                                  lane, warp, nw);
     } else {
       // shared-atomic mode (many bins): all warps work on one tree at a time,
       // splitting its chunks, and add into the job's shared counts
@@ -449,31 +198,14 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalArgs a) {
     __syncthreads();
   }
   if (staged && threadIdx.x == 0) mbar_wait_bounded(&mbar, phase, a.status);  // never left in flight
-  if (cur_job >= 0) flush(jv);
+  if (cur_job >= 0) flush_job(jv, cnt_s, LK, blockDim.x);
+  take_ticket<D>(a, smem, lay.total);
 }
 
 template <int W, int D, int MODE, int Q>
 int launch_t(deoct_ctx* ctx, const EvalArgs& args, const EvalConfig& cfg, size_t smem,
              cudaStream_t s) {
-  auto kern = eval_kernel<W, D, MODE, Q>;
-  DEOCT_TRY(set_max_dynamic_smem(ctx, kern));
-  // all of the unified L1/shared array as shared memory, so that the occupancy
-  // computed below is the residency the launch gets
-  DEOCT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-  int grid = cfg.grid;
-  if (grid <= 0) {
-    int occ = 0;
-    DEOCT_CUDA_TRY(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cfg.warps * 32, smem));
-    if (occ < 1) return set_error(DEOCT_ERR_INVALID, "evaluator tile does not fit: %zu B smem", smem);
-    grid = occ * ctx->num_sms;
-  }
-  if ((int64_t)grid > args.total_tiles) grid = (int)args.total_tiles;
-  if (grid < 1) return DEOCT_OK;
-  kern<<<grid, cfg.warps * 32, smem, s>>>(args);
-  count_launch(ctx);
-  return check_launch("eval_kernel");
+  return launch_kernel(ctx, eval_kernel<W, D, MODE, Q>, args, cfg, smem, s, "eval_kernel");
 }
 
 template <int W, int D>
@@ -557,12 +289,28 @@ void eval_build_jobs(const std::vector<int64_t>& counts, const std::vector<int>&
   *total_tiles = tb;
 }
 
-static size_t eval_smem(int mode, int W, int D, int S, int TG, int F, int K, int warps) {
-  return smem_layout(mode, W, D, S, TG, F, K, warps).total;
-}
-
 static int eval_mode(int D, int K) { return ((1 << D) * K <= 32 * kQMax && D <= 5) ? 0 : 1; }
-int eval_counting_mode(int D, int K) { return eval_mode(D, K); }
+
+// Ballot mode runs on the streaming kernel for groups of fewer than 16 trees
+// (HBM sets the pace there).  Groups of 16+ trees keep the re-laid kernel: its
+// single landing zone leaves room for twice the tile of the streaming ring
+// (measured on GB300: HIGGS-shaped uint32 data, F = 28, ran 1.6x slower on the
+// ring's smaller tiles).
+static bool use_stream(int mode, int W, int TG) { (void)W; return mode == 0 && TG < 16; }
+
+// Landing zones the streaming kernel wants: three for small groups (HBM-bound),
+// two for 16+ trees (the next tile flies while this one is routed).
+static int want_stages(int TG) { return TG < 16 ? kMaxStages : 2; }
+
+// Shared memory of a shape with `nstage` landing zones on the streaming kernel
+// (0: as many as it wants; the re-laid kernel always has its tile and one
+// landing zone).
+static size_t eval_smem(int mode, int W, int D, int S, int TG, int F, int K, int warps,
+                        int nstage = 0, int lab_stage = 1) {
+  if (use_stream(mode, W, TG))
+    return stream_layout(W, D, S, TG, F, K, nstage ? nstage : want_stages(TG), lab_stage).total;
+  return smem_layout(mode, W, D, S, TG, F, K, warps, lab_stage).total;
+}
 
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob) {
@@ -591,13 +339,25 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
     while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && (c.S > 256 || c.TG > 16)) {
       if (c.S > 256) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
     }
-    c.warps = std::max(4, std::min(16, c.TG));  // a warp owns a tree
+    // a warp owns a tree; groups smaller than 16 trees split each tree's chunk
+    // pairs over the warps and run on the streaming kernel, where (measured on
+    // GB300, n = 1e7, P = 1..8) tiles of 1024 samples and 9 warps -- 8 routing
+    // warps and the producer -- keep the most tiles in flight per SM
+    c.warps = 16;
+    if (use_stream(mode, W, c.TG) && c.TG < 16) {
+      c.warps = 9;
+      c.S = std::min(c.S, 1024);
+    }
   } else {
     // shared-atomic mode: the 16 warps split the chunks of one tree at a time, so
-    // the tile keeps at least 16 chunks and the job's counts ([TG][2^D K]) set TG
+    // the tile keeps at least 16 chunks (512 samples); the tile shrinks to that
+    // before the group does, since every tree of a group reuses the staged tile
+    // (wide uint32 data would otherwise end at one tree per group and restage
+    // each tile once per tree), and the job's counts ([TG][2^D K]) set TG
     c.S = 1024;
     c.warps = 16;
     c.TG = std::min(P, 256);
+    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && c.S > 512) c.S /= 2;
     while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && c.TG > 1) c.TG /= 2;
     while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && c.S > 128) c.S /= 2;
     while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && c.TG > 1) c.TG /= 2;
@@ -628,8 +388,31 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
   a.Fmax = plan.Fmax;
   a.Kmax = plan.Kmax;
   a.status = ctx->d_status;
-  const size_t smem = eval_smem(mode, W, D, cfg.S, cfg.TG, plan.Fmax, plan.Kmax, cfg.warps);
-  if (smem > (size_t)ctx->max_smem_optin)
+  a.ticket = plan.d_probs == nullptr ? plan.ticket : nullptr;
+  a.counts_out = plan.counts_out;
+  a.errors_out = plan.errors_out;
+  // Shared memory: the deepest landing-zone ring (streaming kernel: three
+  // zones for small groups, two otherwise) that keeps two CTAs per SM, else
+  // the deepest that fits one CTA; forced shapes that fit in no other way
+  // drop the label landing zones (labels then come by plain loads).
+  const bool streaming = use_stream(mode, W, cfg.TG);
+  const size_t cap = (size_t)ctx->max_smem_optin - 1024;  // room for the static shared memory
+  const size_t two_per_sm = std::min(cap, (size_t)(ctx->smem_per_sm - 2 * 1024) / 2);
+  auto need = [&](int ns, int lab) {
+    return eval_smem(mode, W, D, cfg.S, cfg.TG, plan.Fmax, plan.Kmax, cfg.warps, ns, lab);
+  };
+  const int want = streaming ? want_stages(cfg.TG) : 1;
+  a.nstage = 0;
+  a.lab_stage = 1;
+  for (size_t lim : {two_per_sm, cap})
+    for (int ns = want; ns >= 1 && a.nstage == 0; --ns)
+      if (need(ns, 1) <= lim) a.nstage = ns;
+  if (a.nstage == 0) {
+    a.nstage = 1;
+    a.lab_stage = 0;
+  }
+  const size_t smem = need(a.nstage, a.lab_stage);
+  if (smem > cap)
     return set_error(DEOCT_ERR_INVALID, "evaluator needs %zu B shared memory (F=%d)", smem,
                      plan.Fmax);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -642,8 +425,11 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
     DEOCT_CUDA_TRY(cudaEventRecord(e0, stream));
   }
   const int Q = ((1 << D) * plan.Kmax + 31) / 32;
-  int rc = (W == 2) ? dispatch_depth<2>(ctx, D, mode, Q, a, cfg, smem, stream)
-                    : dispatch_depth<4>(ctx, D, mode, Q, a, cfg, smem, stream);
+  EvalConfig scfg = cfg;  // the streaming kernel has a producer warp and >= 1 routing warp
+  if (scfg.warps < 2) scfg.warps = 2;
+  int rc = streaming ? launch_stream(ctx, W, D, Q, a, scfg, smem, stream)
+           : (W == 2) ? dispatch_depth<2>(ctx, D, mode, Q, a, cfg, smem, stream)
+                      : dispatch_depth<4>(ctx, D, mode, Q, a, cfg, smem, stream);
   if (rc != DEOCT_OK) return rc;
   ctx->eval_launches += 1;
   if (timed) {

@@ -21,6 +21,12 @@ struct EvalProb {
   int64_t start;           // first sample of the segment (into idx, or a column)
   int64_t count;           // samples in the segment
   int32_t F, K, P, tma;    // tma: rank rows may be staged with 1-D bulk copies
+  int32_t lab_tma = 0;     // labels + start is 16-byte aligned: labels staged by bulk copy too
+  // nullable: the trees as given by the caller (a [P][B], 0 = no split; theta
+  // [P][B]), validated and packed while a job's node table is built; `nodes`
+  // is unused then
+  const uint16_t* a16 = nullptr;
+  const uint32_t* th32 = nullptr;
 };
 // A job is one tree group of one problem; its tiles are contiguous in the
 // flattened tile order that the persistent CTAs split evenly.
@@ -48,6 +54,12 @@ struct EvalPlan {
   int64_t total_tiles = 0;
   int Fmax = 0, Kmax = 0, Pmax = 0;
   int64_t max_count = 0;
+  // single problem only: `single.counts` is an accumulator that is zero at
+  // rest and `ticket` a zero-at-rest counter; the last CTA to finish writes
+  // errors_out / counts_out (each nullable), zeroes both again
+  uint32_t* ticket = nullptr;
+  uint32_t* counts_out = nullptr;
+  uint32_t* errors_out = nullptr;
 };
 
 int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalConfig& cfg,
@@ -55,8 +67,6 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
 // Choose S / TG / warps for a workload shape (heuristic, tuned by measurement).
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob);
-// 0: ballot counting (2^D K <= 128, D <= 5); 1: shared-memory atomics
-int eval_counting_mode(int D, int K);
 // build the job list for host-side problems (tile counts per problem)
 void eval_build_jobs(const std::vector<int64_t>& counts, const std::vector<int>& pops, int S,
                      int TG, std::vector<EvalJob>* jobs, int64_t* total_tiles);

@@ -537,6 +537,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     e.K = K;
     e.P = P;
     e.tma = 1;
+    e.lab_tma = (reinterpret_cast<uintptr_t>(c.clabels + e.start) % 16 == 0) ? 1 : 0;
   }
   DEProb* ddp = nullptr;
   EvalProb* dep = nullptr;
@@ -576,14 +577,14 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   if (!have && !forced) {
     // candidates around the heuristic; each runs the real evaluation of S^1
     std::vector<EvalConfig> cands;
-    const int cmode = eval_counting_mode(Dt, K);
     for (int S : {256, 512, 1024, 2048})
       for (int TG : {cfg.TG, std::max(1, cfg.TG / 2), P}) {
         EvalConfig x = cfg;
         x.S = S;
         x.TG = std::min(TG, P);
-        // ballot counting: a warp owns a tree; shared atomics: warps split a tree's chunks
-        x.warps = cmode == 0 ? std::max(4, std::min(16, x.TG)) : 16;
+        // ballot counting: a warp owns a tree (small groups split a tree's chunk
+        // pairs over warps); shared atomics: warps split a tree's chunks
+        x.warps = 16;
         bool dup = false;
         for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG);
         if (!dup) cands.push_back(x);

@@ -115,6 +115,7 @@ extern "C" DEOCT_API int deoct_eval_population_noalloc(const deoct_dataset* ds,
       const bool aligned = (reinterpret_cast<uintptr_t>(ds->ranks) % 16 == 0) &&
                            ((ds->ld * ds->rank_bytes) % 16 == 0);
       p.tma = (sample_idx == nullptr && aligned) ? 1 : 0;
+      p.lab_tma = (p.tma && reinterpret_cast<uintptr_t>(ds->labels) % 16 == 0) ? 1 : 0;
       plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
       plan.Fmax = ds->F;
       plan.Kmax = ds->K;

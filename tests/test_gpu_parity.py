@@ -356,3 +356,44 @@ def test_eval_with_unaligned_row_stride(c, rb, extra):
     a, th = datagen.random_population(nu_ref, P, depth, rng, allow_nosplit=True)
     counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
     np.testing.assert_array_equal(u32(counts), oracle.eval_counts(r_ref, y, K, a, th, depth))
+
+
+@pytest.mark.parametrize("lab_off", [0, 1, 16])
+def test_eval_is_one_launch_and_leaves_no_state(c, lab_off):
+    """An evaluation of caller trees is one kernel launch: the trees are packed while the node
+    tables are built, and the last CTA to finish writes errors and counts and zeroes its
+    accumulator again.  Growing and shrinking shapes, both counting modes, errors-only calls,
+    an invalid tree, and labels at any byte offset (bulk-copied when 16-byte aligned, else read
+    with plain loads; n is not a multiple of 16) leave every next result exact."""
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(777 + lab_off)
+    n, F, K = 30001, 7, 3
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    base = gpu_dataset(c, X, y, K, 2)
+    ybuf = torch.zeros(n + 32, dtype=torch.uint8, device="cuda")
+    ybuf[lab_off:lab_off + n] = to_dev(y)
+    ds = deoct.DeviceDataset(base.ranks, 2, base.n_unique, ybuf[lab_off:lab_off + n], n, F, K)
+    for P, depth in [(37, 3), (300, 4), (9, 2), (300, 4), (5, 7)]:
+        a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+        ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+        _, ref_err, _, _ = oracle.fitness(ref, a, n)
+        c.reset_stats()
+        counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+        assert c.stats()["launches"] == 1
+        np.testing.assert_array_equal(u32(counts), ref)
+        np.testing.assert_array_equal(u32(errors), ref_err)
+        _, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth,
+                                                want_counts=False)
+        np.testing.assert_array_equal(u32(errors), ref_err)
+    # an invalid tree is reported by the next sync call and leaves nothing behind
+    bad = a.astype(np.uint16)
+    bad[0, 0] = F + 2
+    deoct.deoct_eval_population(c, ds, to_dev(bad), to_dev(th), depth)
+    with pytest.raises(deoct.DeoctError):
+        deoct.deoct_depth1_search(c, ds)
+    counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+    np.testing.assert_array_equal(u32(counts), ref)
+    np.testing.assert_array_equal(u32(errors), ref_err)
