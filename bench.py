@@ -42,14 +42,14 @@ WORKLOAD = dict(workload="large-deoct: n=1e7, F=10 U(0,1) quantised to 60000 lev
 INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # DRAM bytes (read + write) of one evaluator launch on this workload, from the ncu
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
-# kernel source it was taken on (hash of csrc/eval.cu + csrc/common.cuh).
+# kernel source it was taken on (hash of csrc/eval.cu, eval_kernel.cuh, common.cuh).
 EVAL_TRAFFIC = {"source_sha256_16": "077e1c84bf5273dc", "bytes": 378_726_912 + 3_900_928}
 
 
 def _eval_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("eval.cu", "common.cuh"):
+    for f in ("eval.cu", "eval_kernel.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2311_06952_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -389,6 +389,48 @@ def eval_p_sweep(ctx, ranks, nu, yd, n, F, K, peaks, depth=4):
             "rows": rows}
 
 
+def run_p_eval(args):
+    """Evaluations of P random depth-4 trees on the main workload's ranks (n = --n, uint16),
+    one launch each, timed on the evaluator launch; the encoder's scratch is released first,
+    so little else sits on the device (the form profiled for small populations)."""
+    import torch
+    from paper_2311_06952_gb300 import build as _build
+    from paper_2311_06952_gb300 import datagen, deoct
+    _build.build()
+    torch.cuda.set_device(0)
+    data = datagen.make_workload(3, n=args.n)
+    enc = deoct.Context(0)
+    ds = deoct.encode_dataset(enc, torch.from_numpy(data["X"]).cuda(), torch.from_numpy(data["y"]).cuda(), 2, 2)
+    torch.cuda.synchronize()
+    enc.close()
+    torch.cuda.empty_cache()
+    ctx = deoct.Context(0)
+    P = args.p_eval
+    nu = ds.n_unique.cpu().numpy().view(np.uint32)
+    a, th = datagen.random_population(nu, P, 4, np.random.Generator(np.random.PCG64(50 + P)))
+    ad = torch.from_numpy(a.astype(np.int16)).cuda()
+    td = torch.from_numpy(th.view(np.int32)).cuda()
+    ms = []
+    for it in range(args.warmup + args.steps):
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        counts, errs = deoct.deoct_eval_population(ctx, ds, ad, td, 4)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        ctx.set_timing(False)
+        if it >= args.warmup:
+            ms.append(st["eval_ms"] / max(1, st["eval_timed"]))
+    n, F = data["X"].shape
+    m = float(np.median(ms))
+    peaks, kind = _peaks()
+    gbs = n * (2 * F + 1) / (m / 1000.0) / 1e9
+    print(json.dumps({"mode": "p-eval", "P": P, "n": n, "launch_ms": m, "evals_per_s": P * n / (m / 1000.0),
+                      "alg_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"], "peak_kind": kind,
+                      "errors0": int(errs[0])}), flush=True)
+    ctx.close()
+    return 0
+
+
 PAPER_TABLE3_S = {  # MH-DEOCT training time on an A100 (Table 3), seconds, D = 2 / 4 / 8
     "bitcoin-heist": (77.22, 259.98, 1633.93), "susy": (164.03, 399.88, 5100.47),
     "higgs": (333.01, 1049.87, 15885.24)}
@@ -569,6 +611,7 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--table3", default="", help="comma list of bitcoin-heist,susy,higgs")
     ap.add_argument("--mh-only", action="store_true", help="only the batched-vs-plain moving-horizon line")
+    ap.add_argument("--p-eval", type=int, default=0, help="only single evaluations of this many trees")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -576,6 +619,8 @@ def main():
         return run_serve(args)
     if args.table3:
         return run_table3(args)
+    if args.p_eval:
+        return run_p_eval(args)
     if args.mh_only:
         import torch
         torch.cuda.set_device(0)

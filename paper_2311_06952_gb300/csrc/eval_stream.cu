@@ -59,9 +59,9 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const EvalArgs a) {
     JobView pv;
     int64_t i = 0;
     uint32_t issued = 0;  // bit z: zone z was staged at least once
+    int z = 0;            // i % NS
+    uint32_t round = 0;   // i / NS
     for (int64_t pt = t0; pt < t1; ++pt, ++i) {
-      const int z = (int)(i % NS);
-      const uint32_t round = (uint32_t)(i / NS);
       if (round > 0) {
         int ok = 1;
         if (lane == 0) ok = mbar_wait_bounded(&empty[z], (round - 1) & 1u, a.status) ? 1 : 0;
@@ -88,24 +88,27 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const EvalArgs a) {
       }
       issued |= 1u << z;
       __syncwarp();
+      if (++z == NS) {
+        z = 0;
+        ++round;
+      }
     }
     // every staged zone's last phase has completed (landed) before the CTA
     // leaves: waits that are already satisfied return at once
     if (lane == 0)
-      for (int z = 0; z < NS; ++z)
-        if (issued & (1u << z)) {
-          // zone z was last staged in round r = the largest with r NS + z < i
-          const uint32_t r = (uint32_t)((i - 1 - z) / NS);
-          mbar_wait_bounded(&full[z], r & 1u, a.status);
+      for (int q = 0; q < NS; ++q)
+        if (issued & (1u << q)) {
+          // zone q was last staged in round r = the largest with r NS + q < i
+          const uint32_t r = (uint32_t)((i - 1 - q) / NS);
+          mbar_wait_bounded(&full[q], r & 1u, a.status);
         }
   } else {
     // ---- consumers: route tile t0 + i from zone i % NS ---------------------
     uint32_t cst[Q][D];  // per owned bin, "right" (0) or "left" (~0) at level d
     int K = 0;
-    int64_t i = 0;
-    for (int64_t gt = t0; gt < t1; ++gt, ++i) {
-      const int z = (int)(i % NS);
-      const uint32_t ph = (uint32_t)(i / NS) & 1u;
+    int z = 0;        // zone of tile gt: (gt - t0) % NS
+    uint32_t ph = 0;  // parity of its phase: ((gt - t0) / NS) & 1
+    for (int64_t gt = t0; gt < t1; ++gt) {
       JobView nv;  // job and tile of gt: a search at the first tile, then a step
       if (gt == t0) {
         lookup_job(a, gt, &nv);
@@ -161,6 +164,10 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const EvalArgs a) {
                                  nodes_sa, aux_sa, cst, cnt_s, LK, lane, warp, ncw);
       bar_sync_n(nct);
       if (threadIdx.x == 0) mbar_arrive(&empty[z]);  // the producer may restage zone z
+      if (++z == NS) {
+        z = 0;
+        ph ^= 1u;
+      }
     }
   }
   __syncthreads();

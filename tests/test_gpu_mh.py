@@ -68,6 +68,11 @@ def _mh_case(name):
         X = np.round(rng.random((5000, 5)), 2).astype(np.float32)
         y = datagen.planted_tree_labels(X, 3, 3, rng)
         return X, y, 3, dict(depth=4, horizon=3, P=16, G=6, seed=9, n_min=30, alpha=0.5), 2
+    if name == "small_pop":
+        # 6 individuals per node: every evaluator shape the batched level tries
+        # has fewer than 16 trees per group (the streaming kernel)
+        w = datagen.make_workload(2, n=20000)
+        return w["X"], w["y"], w["K"], dict(depth=5, horizon=3, P=6, G=5, seed=5), 2
     if name == "horizon1":
         rng = _rng(42)
         X = np.round(rng.random((3000, 4)), 2).astype(np.float32)
@@ -76,7 +81,8 @@ def _mh_case(name):
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["w0_d2h2", "w0_d3h2", "w2_small", "k3_d4h3_nmin", "horizon1"])
+@pytest.mark.parametrize("name", ["w0_d2h2", "w0_d3h2", "w2_small", "k3_d4h3_nmin", "small_pop",
+                                  "horizon1"])
 @pytest.mark.parametrize("batched", [False, True])
 def test_moving_horizon_bit_exact(c, name, batched):
     from paper_2311_06952_gb300 import deoct

@@ -397,3 +397,37 @@ def test_eval_is_one_launch_and_leaves_no_state(c, lab_off):
     counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
     np.testing.assert_array_equal(u32(counts), ref)
     np.testing.assert_array_equal(u32(errors), ref_err)
+
+
+@pytest.mark.parametrize("depth,K", [(4, 2), (3, 5), (5, 3)])
+@pytest.mark.parametrize("rb", [2, 4])
+def test_eval_small_groups_streaming_bit_exact(c, depth, K, rb):
+    """Groups of fewer than 16 trees run on the streaming kernel (a producer warp keeps a ring of
+    landing zones filled; routing warps read the natural sample order).  P = 1, 2, 5, 15 on all
+    samples and on a gathered subset; the default grid (about one tile per CTA here) and a grid
+    of 7 CTAs that cycles each ring many times; 1, 2 and 3 bins per lane; a ragged tail."""
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(900 + 10 * depth + K + rb)
+    n, F = 200_003, 7
+    X = np.round(rng.random((n, F)), 4).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    ds = gpu_dataset(c, X, y, K, rb)
+    idx = np.sort(rng.permutation(n)[: n // 3]).astype(np.int32)
+    for P in (1, 2, 5, 15):
+        a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+        ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+        ref_sub = oracle.eval_counts(ranks, y, K, a, th, depth, idx=idx)
+        _, ref_err, _, _ = oracle.fitness(ref, a, n)
+        for grid in (0, 7):
+            try:
+                c.set_eval_config(0, 0, 0, grid)
+                counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)),
+                                                             to_dev(th), depth)
+                np.testing.assert_array_equal(u32(counts), ref)
+                np.testing.assert_array_equal(u32(errors), ref_err)
+                counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th),
+                                                        depth, sample_idx=to_dev(idx))
+                np.testing.assert_array_equal(u32(counts), ref_sub)
+            finally:
+                c.set_eval_config(0, 0, 0, 0)
