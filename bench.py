@@ -43,7 +43,7 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # DRAM bytes (read + write) of one evaluator launch on this workload, from the ncu
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
 # kernel source it was taken on (hash of csrc/eval.cu, eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "077e1c84bf5273dc", "bytes": 378_726_912 + 3_900_928}
+EVAL_TRAFFIC = {"source_sha256_16": "861fbfc194f38c3c", "bytes": 360_715_520 + 3_927_552}
 
 
 def _eval_source_hash():
