@@ -323,30 +323,47 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
     return per * nprob * ((P + TG - 1) / TG);
   };
   if (mode == 0) {
-    // measured on GB300 (n = 1e7, F = 10, depth 4, P = 1024): 16 warps per CTA and
-    // two CTAs per SM beat 8 warps by 1.5x; tiles of 1024 samples with 256 trees
-    // per job were the fastest shape that leaves room for two CTAs
-    c.S = 2048;
-    c.TG = std::min(P, 256);
     c.warps = 16;
-    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && (c.S > 512 || c.TG > 32)) {
-      if (c.S > 512) c.S /= 2; else c.TG /= 2;
-    }
-    while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && (c.S > 128 || c.TG > 1)) {
-      if (c.S > 128) c.S /= 2; else c.TG = std::max(1, c.TG / 2);
-    }
-    // enough independent tiles to fill the GPU for small problems
-    while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && (c.S > 256 || c.TG > 16)) {
-      if (c.S > 256) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
-    }
-    // a warp owns a tree; groups smaller than 16 trees split each tree's chunk
-    // pairs over the warps and run on the streaming kernel, where (measured on
-    // GB300, n = 1e7, P = 1..8) tiles of 1024 samples and 9 warps -- 8 routing
-    // warps and the producer -- keep the most tiles in flight per SM
-    c.warps = 16;
-    if (use_stream(mode, W, c.TG) && c.TG < 16) {
+    if (P < 16) {
+      // small groups run on the streaming kernel, where (measured on GB300,
+      // n = 1e7, P = 1..8) tiles of 1024 samples and 9 warps -- 8 routing warps
+      // and the producer -- keep the most tiles in flight per SM
+      c.TG = P;
+      c.S = 1024;
       c.warps = 9;
-      c.S = std::min(c.S, 1024);
+      while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && c.S > 256) c.S /= 2;
+      while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && c.S > 256) c.S /= 2;
+    } else {
+      // A warp owns a tree; 16 warps per CTA and two CTAs per SM (measured on
+      // GB300: 1.5x faster than 8 warps).  Among the shapes that keep two CTAs
+      // per SM, take the least estimated makespan: waves of work items (S
+      // samples x TG trees) over the resident CTAs, each costing its S TG
+      // evaluations plus a staging overhead worth about 7000 + 170 F evaluations
+      // (tile copies, masks, node tables; fitted to shape sweeps at n = 1e5,
+      // F = 20 and n = 1e7, F = 10).  Few large items leave CTAs idle in the
+      // last wave; many small ones pay the overhead.
+      const int64_t ncta = 2 * (int64_t)ctx->num_sms;
+      double best = -1.0;
+      for (int S : {2048, 1024, 512, 256})
+        for (int TG : {256, 128, 64, 32, 16}) {
+          const int tg = std::min(TG, P);
+          if (tg < 16 || eval_smem(mode, W, D, S, tg, F, K, 16) > two_per_sm) continue;
+          const int64_t items = work(S, tg);
+          const double waves = (double)((items + ncta - 1) / ncta);
+          const double cost = waves * ((double)S * tg + 7000.0 + 170.0 * F);
+          if (best < 0 || cost < best) {
+            best = cost;
+            c.S = S;
+            c.TG = tg;
+          }
+        }
+      if (best < 0) {  // nothing keeps two CTAs per SM: the largest shape that fits
+        c.S = 2048;
+        c.TG = std::min(P, 256);
+        while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > (size_t)limit && (c.S > 128 || c.TG > 16)) {
+          if (c.S > 128) c.S /= 2; else c.TG = std::max(16, c.TG / 2);
+        }
+      }
     }
   } else {
     // shared-atomic mode: the 16 warps split the chunks of one tree at a time, so
