@@ -44,7 +44,11 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
 # kernel source it was taken on: a hash of the re-laid evaluator kernel's text in
 # csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "d18f10b12f798a39", "bytes": 360_715_520 + 3_927_552}
+EVAL_TRAFFIC = {"source_sha256_16": "d18f10b12f798a39", "bytes": 360_715_520 + 3_927_552,
+                # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
+                "ncu": {"inst_per_cycle": 3.177, "issue_frac": 3.177 / 4.0, "alu_pipe_frac": 0.7256,
+                        "shared_pipe_frac": 0.80, "inst_per_chunk": 36.2, "dram_gbs": 31.2,
+                        "dram_frac_of_peak": 0.0039}}
 
 
 def _eval_source_hash():
@@ -63,6 +67,10 @@ def _eval_source_hash():
 
 def _traffic_default():
     return EVAL_TRAFFIC["bytes"] if _eval_source_hash() == EVAL_TRAFFIC["source_sha256_16"] else None
+
+
+def _ncu_default():
+    return EVAL_TRAFFIC["ncu"] if _eval_source_hash() == EVAL_TRAFFIC["source_sha256_16"] else None
 
 
 def _peaks():
@@ -578,6 +586,7 @@ def run_ours(args):
                      "ops_per_launch": ops_per_launch, "launch_ms": eval_ms,
                      "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz (%s max clock)" % (
                          nsm, INT32_LANES_PER_SM, sm_mhz, peak_kind),
+                     "issue_view": _ncu_default() if args.n == WORKLOAD["n"] else None,
                      "hbm_view": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"],
                                   "frac": hbm_achieved / peaks["hbm_gbs"],
                                   "algorithmic_bytes_per_launch": bytes_per_launch,

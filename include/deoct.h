@@ -175,7 +175,11 @@ DEOCT_API int deoct_decode_population(deoct_ctx* ctx, const deoct_dataset* ds, c
  *             reported by the next sync call, and the node then routes right
  *  counts_out [P][2^depth][K] uint32, or NULL
  *  errors_out [P] uint32, or NULL
- * async. */
+ * One kernel launch when n_sub > 0: the trees are validated and packed as the
+ * evaluator builds its node tables, and its last CTA writes errors_out and
+ * counts_out from an accumulator in the context's scratch that is zero again
+ * when the launch ends.  Calls on one context must therefore be ordered on one
+ * stream (two streams sharing a context race on that scratch).  async. */
 DEOCT_API int deoct_eval_population(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* sample_idx,
                           int64_t n_sub, const uint16_t* a, const uint32_t* theta, int32_t P,
                           int32_t depth, uint32_t* counts_out, uint32_t* errors_out,
