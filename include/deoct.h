@@ -130,6 +130,16 @@ DEOCT_API int deoct_reset_stats(deoct_ctx* ctx);
  * the next evaluation. */
 DEOCT_API int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, int32_t grid);
 
+/* Self-test of the library's failure detection (no counterpart in the paper).
+ * Every device-side wait of the library (the evaluator's mbarrier waits) is
+ * bounded and, when it runs out, sets a bit in the context's status word that
+ * the next sync call reports as DEOCT_ERR_TIMEOUT, leaving the context usable.
+ * This call launches one warp that waits on an mbarrier nothing arrives on, for
+ * `tries` hinted tries of up to ~1 us each (1 <= tries <= 2^20), then returns
+ * what the sync check reports: DEOCT_ERR_TIMEOUT when the mechanism works.
+ * sync. */
+DEOCT_API int deoct_selftest_wait(deoct_ctx* ctx, int32_t tries, void* stream);
+
 /* ---- a1: rank encoder ----------------------------------------------------
  * Section 3.1: the threshold set B_p of feature p is built from its sorted
  * unique values; a sample's position among them (its dense rank) decides every

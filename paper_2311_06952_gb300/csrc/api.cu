@@ -422,6 +422,35 @@ int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, 
   API_END
 }
 
+namespace deoct {
+namespace {
+// One warp waits on an mbarrier that nothing arrives on: lane 0's bounded wait
+// runs out and records ST_TIMEOUT.
+__global__ void selftest_wait_kernel(uint32_t tries, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (threadIdx.x == 0) mbar_wait_tries(&bar, 0u, tries, status);
+  __syncwarp();
+}
+}  // namespace
+}  // namespace deoct
+
+int deoct_selftest_wait(deoct_ctx* ctx, int32_t tries, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  if (tries < 1 || tries > (1 << 20)) return set_error(DEOCT_ERR_INVALID, "tries = %d", tries);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  selftest_wait_kernel<<<1, 32, 0, s>>>((uint32_t)tries, ctx->d_status);
+  count_launch(ctx);
+  DEOCT_TRY(check_launch("selftest_wait_kernel"));
+  return check_status(ctx, s);
+  API_END
+}
+
 int deoct_encode(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_t rank_bytes,
                  void* ranks_out, int64_t ld, uint32_t* n_unique_out, void* stream) {
   return deoct_encode_ex(ctx, X, n, F, rank_bytes, ranks_out, ld, n_unique_out, nullptr, stream);

@@ -179,13 +179,18 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
       : "memory");
   return ok != 0;
 }
-// Bounded wait: at most 2^20 hinted tries of up to 1 us each (order of a
-// second), then records ST_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
-  for (uint32_t it = 0; it < (1u << 20); ++it)
+// Bounded wait: at most `tries` hinted tries of up to 1 us each, then records
+// ST_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_tries(uint64_t* bar, uint32_t parity, uint32_t tries,
+                                                int* status) {
+  for (uint32_t it = 0; it < tries; ++it)
     if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
   atomicOr(status, ST_TIMEOUT);
   return false;
+}
+// The library's waits: 2^20 tries (order of a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+  return mbar_wait_tries(bar, parity, 1u << 20, status);
 }
 // 1-D TMA bulk copy global -> shared, completion counted on `bar` in bytes.
 // dst, src 16-byte aligned; bytes a multiple of 16.

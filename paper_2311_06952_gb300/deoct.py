@@ -34,6 +34,7 @@ EXPORTED = [
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
     "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
     "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
+    "deoct_selftest_wait",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -89,6 +90,7 @@ def load(path: str | None = None):
             "deoct_get_stats": [_vp, ctypes.POINTER(Stats)],
             "deoct_reset_stats": [_vp],
             "deoct_set_eval_config": [_vp, _i32, _i32, _i32, _i32],
+            "deoct_selftest_wait": [_vp, _i32, _vp],
             "deoct_encode": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp],
             "deoct_encode_ex": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
             "deoct_split_values": [_vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp],
@@ -185,6 +187,12 @@ class Context:
 
     def reset_stats(self):
         _check(load().deoct_reset_stats(self.handle))
+
+    def selftest_wait(self, tries=1000, stream=None):
+        """One warp waits on an mbarrier nothing arrives on, for `tries` tries of up
+        to ~1 us; returns the status code the sync check reports (DEOCT_ERR_TIMEOUT
+        when bounded waits work) and leaves the context usable."""
+        return int(load().deoct_selftest_wait(self.handle, int(tries), _stream(stream)))
 
     def set_eval_config(self, S=0, TG=0, warps=0, grid=0):
         """Force the evaluator's launch shape (0 = automatic); results are unchanged."""

@@ -431,3 +431,22 @@ def test_eval_small_groups_streaming_bit_exact(c, depth, K, rb):
                 np.testing.assert_array_equal(u32(counts), ref_sub)
             finally:
                 c.set_eval_config(0, 0, 0, 0)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers(c):
+    """Failure detection without a fault: a device wait on an mbarrier that nothing arrives on
+    runs out after its bound, the next sync check reports DEOCT_ERR_TIMEOUT and clears the
+    status word, and the context keeps evaluating correctly."""
+    from paper_2311_06952_gb300 import deoct
+    assert c.selftest_wait(2000) == deoct.DEOCT_ERR_TIMEOUT
+    assert c.selftest_wait(1) == deoct.DEOCT_ERR_TIMEOUT
+    rng = _rng(1234)
+    n, F, K, depth, P = 5000, 5, 3, 3, 20
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    ds = gpu_dataset(c, X, y, K, 2)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+    np.testing.assert_array_equal(u32(counts), oracle.eval_counts(ranks, y, K, a, th, depth))
+    deoct.deoct_depth1_search(c, ds)  # a sync call: no status left behind
