@@ -450,3 +450,52 @@ def test_bounded_wait_timeout_is_reported_and_context_recovers(c):
     counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
     np.testing.assert_array_equal(u32(counts), oracle.eval_counts(ranks, y, K, a, th, depth))
     deoct.deoct_depth1_search(c, ds)  # a sync call: no status left behind
+
+
+MAX_CASES = [
+    # n, F, K, depth, P, rank_bytes -- each at one of the header's limits
+    (3000, 256, 2, 3, 40, 4),      # F = 256 features, uint32 rows: the widest tile
+    (3000, 256, 3, 2, 20, 2),      # F = 256, uint16 rows (re-laid tile)
+    (5000, 4, 255, 2, 16, 2),      # K = 255 classes: shared-atomic mode, 1020 bins
+    (5000, 4, 2, 10, 8, 4),        # depth 10: 1023 nodes, 2048 bins
+    (2000, 3, 2, 3, 4096, 2),      # P = 4096 trees: 16 tree groups
+]
+
+
+@pytest.mark.parametrize("case", MAX_CASES, ids=[str(x) for x in MAX_CASES])
+def test_eval_maximum_sizes_bit_exact(c, case):
+    """The evaluator at the header's limits on F, K, depth and P matches the oracle."""
+    from paper_2311_06952_gb300 import deoct
+    n, F, K, depth, P, rb = case
+    rng = _rng(1500 + F + K + depth + P)
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ds = gpu_dataset(c, X, y, K, rb)
+    ranks, nu = oracle.encode(X)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+    _, ref_err, _, _ = oracle.fitness(ref, a, n)
+    np.testing.assert_array_equal(u32(counts), ref)
+    np.testing.assert_array_equal(u32(errors), ref_err)
+
+
+def test_encode_and_eval_at_max_samples(c):
+    """n = 2^24 samples of one feature, all values distinct: ranks and thresholds reach the
+    24-bit packing limit (theta up to 2^24 - 1)."""
+    from paper_2311_06952_gb300 import deoct
+    n = 1 << 24
+    rng = _rng(1600)
+    X = (rng.permutation(n).astype(np.float64) * 0.5 - 1000.0).astype(np.float32)[:, None]
+    y = rng.integers(0, 2, n).astype(np.uint8)
+    ds = gpu_dataset(c, X, y, 2, 4)
+    ranks, nu = oracle.encode(X)
+    assert int(nu[0]) == n
+    np.testing.assert_array_equal(ranks_np(ds), ranks)
+    a = np.ones((3, 3), np.int32)
+    th = np.array([[n - 1, 5, n // 2], [0, n - 1, 1], [n // 3, n // 4, n - 2]], np.uint32)
+    counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), 2)
+    ref = oracle.eval_counts(ranks, y, 2, a, th, 2)
+    _, ref_err, _, _ = oracle.fitness(ref, a, n)
+    np.testing.assert_array_equal(u32(counts), ref)
+    np.testing.assert_array_equal(u32(errors), ref_err)
