@@ -1,6 +1,7 @@
 // common.cuh -- shared internals of libdeoct (context, errors, PTX helpers, Philox).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -200,6 +201,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// 2-D tiled TMA copy global -> shared of the box at element coordinates (x, y)
+// of the tensor map `tmap` (a __grid_constant__ kernel parameter); the box
+// lands densely, row-major; columns past the tensor's width read as zero.
+// x * element size must be a multiple of 16 bytes; dst 128-byte aligned.
+__device__ __forceinline__ void bulk_tensor_2d_g2s(void* dst, const void* tmap, int x, int y,
+                                                   uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 

@@ -8,6 +8,8 @@
 // conflicts; the next tile's bulk copies fly while the current one is routed.
 // It also holds the shared-atomic counting mode for 2^D K > 128 bins: all
 // warps split each tree's chunks and add into the job's shared counts.
+#include <cudaTypedefs.h>
+
 #include "eval_kernel.cuh"
 
 namespace deoct {
@@ -17,7 +19,7 @@ using namespace evk;
 namespace {
 
 template <int W, int D, int MODE, int Q>
-__global__ void __launch_bounds__(512, 2) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(512, 2) eval_kernel(const __grid_constant__ EvalArgs a) {
   constexpr int B = (1 << D) - 1;
   constexpr int L = 1 << D;
   typedef typename RankT<W>::T RT;
@@ -84,7 +86,10 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const EvalArgs a) {
     // ---- stage rank rows (and labels) ------------------------------------
     if (P.tma) {
       if (!staged && warp == 0)
-        issue_tile_tma(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane);
+        if (W == 2 && a.tmap_box)
+          issue_tile_boxes(a, P, s0, ns, stageb, lab_land, &mbar, lane);
+        else
+          issue_tile_tma(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane);
     } else {
       const RT* src = static_cast<const RT*>(P.ranks);
       for (int e = threadIdx.x; e < P.F * S; e += blockDim.x) {
@@ -120,13 +125,23 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const EvalArgs a) {
         // stage (natural order) -> tile (chunk-pair interleaved): a task is
         // four tile words of one row, from two 8-byte loads (samples 64p+4m..
         // +3 and 64p+32+4m..+3) and four byte permutes, one 16-byte store
+        // (landing zone: natural rows [F][S], or box-major from the tensor map:
+        // box b of BX samples at b Fmax BX, its row f at f BX -- a chunk pair
+        // never straddles a box)
         const int quads = npair * 8;  // tasks per row
         const int tasks = P.F * quads;
         const int fstep = blockDim.x / quads, qstep = blockDim.x - fstep * quads;
+        const int BX = a.tmap_box, lbx = BX ? __ffs(BX) - 1 : 0;
         int f = threadIdx.x / quads, q = threadIdx.x - f * quads;
         for (int e = threadIdx.x; e < tasks; e += blockDim.x) {
           const int pp = q >> 3, m = q & 7;
-          const unsigned char* srow = stageb + (size_t)f * S * 2 + pp * 128 + m * 8;
+          const unsigned char* srow;
+          if (BX) {
+            const int j0 = pp * 64;
+            srow = stageb + ((size_t)((j0 >> lbx) * a.Fmax + f) * BX + (j0 & (BX - 1))) * 2 + m * 8;
+          } else {
+            srow = stageb + (size_t)f * S * 2 + pp * 128 + m * 8;
+          }
           const uint2 lo = *reinterpret_cast<const uint2*>(srow);
           const uint2 hi = *reinterpret_cast<const uint2*>(srow + 64);
           uint4 o;
@@ -163,7 +178,10 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const EvalArgs a) {
         if (warp == 0) {
           const int64_t xs0 = X.start + xv.tile * (int64_t)S;
           const int64_t xrem = X.start + X.count - xs0;
-          issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, lab_land,
+          if (W == 2 && a.tmap_box)
+            issue_tile_boxes(a, X, xs0, xrem < S ? (int)xrem : S, stageb, lab_land, &mbar, lane);
+          else
+            issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, lab_land,
                          a.lab_stage, &mbar, lane);
         }
         staged = true;
@@ -386,6 +404,56 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
   return c;
 }
 
+// cuTensorMapEncodeTiled from the driver (the runtime hands out its entry point).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The uint16 rows of a plan as one 2-D tensor map ([F] rows of `ncols` columns,
+// row stride ld), boxes of BX columns x F rows; false when the plan's problems
+// do not share one TMA-able rank array or the driver declines.
+static bool encode_rank_map(const EvalPlan& plan, int S, EvalArgs* a) {
+  const void* base = nullptr;
+  int64_t ld = 0, ncols = 0;
+  if (plan.d_probs == nullptr) {
+    if (!plan.single.tma || plan.single.F != plan.Fmax) return false;
+    base = plan.single.ranks;
+    ld = plan.single.ld;
+    ncols = plan.single.ncols;
+  } else {
+    if (!plan.shared_ranks) return false;
+    base = plan.shared_ranks;
+    ld = plan.shared_ld;
+    ncols = plan.shared_ncols;
+  }
+  const int BX = (S % 256 == 0) ? 256 : 128;
+  if (S % BX != 0 || plan.Fmax < 1 || plan.Fmax > 256 || ncols < 1) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 2) % 16 != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ncols, (cuuint64_t)plan.Fmax};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BX, (cuuint32_t)plan.Fmax};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&a->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  a->tmap_box = BX;
+  return true;
+}
+
 int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalConfig& cfg,
                 cudaStream_t stream) {
   if (plan.total_tiles <= 0) return DEOCT_OK;
@@ -442,6 +510,9 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
     DEOCT_CUDA_TRY(cudaEventRecord(e0, stream));
   }
   const int Q = ((1 << D) * plan.Kmax + 31) / 32;
+  // uint16 rows on the re-laid kernel: a tile arrives as S / BX 2-D tensor boxes
+  a.tmap_box = 0;
+  if (W == 2 && !streaming) encode_rank_map(plan, cfg.S, &a);
   EvalConfig scfg = cfg;  // the streaming kernel has a producer warp and >= 1 routing warp
   if (scfg.warps < 2) scfg.warps = 2;
   int rc = streaming ? launch_stream(ctx, W, D, Q, a, scfg, smem, stream)

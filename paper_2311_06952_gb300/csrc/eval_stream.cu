@@ -19,7 +19,7 @@ namespace evk {
 namespace {
 
 template <int W, int D, int Q>
-__global__ void __launch_bounds__(512, 2) eval_stream_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_constant__ EvalArgs a) {
   typedef typename RankT<W>::T RT;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];

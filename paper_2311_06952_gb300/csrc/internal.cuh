@@ -60,6 +60,11 @@ struct EvalPlan {
   uint32_t* ticket = nullptr;
   uint32_t* counts_out = nullptr;
   uint32_t* errors_out = nullptr;
+  // multi-problem plans whose problems all read one rank array (the batched
+  // level solve): that array, its row stride and width, so the launch can
+  // describe it with one TMA tensor map (nullptr: no tensor map)
+  const void* shared_ranks = nullptr;
+  int64_t shared_ld = 0, shared_ncols = 0;
 };
 
 int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalConfig& cfg,

@@ -468,6 +468,11 @@ int build_plan(deoct_ctx* ctx, BatchedEval* be, const EvalConfig& cfg, int F, in
   be->plan.Kmax = K;
   be->plan.Pmax = P;
   be->plan.max_count = mx;
+  if (!be->probs.empty()) {  // every segment reads the one compacted rank array
+    be->plan.shared_ranks = be->probs[0].ranks;
+    be->plan.shared_ld = be->probs[0].ld;
+    be->plan.shared_ncols = be->probs[0].ncols;
+  }
   return DEOCT_OK;
 }
 
