@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const __grid_constant__ Ev
     // ---- stage rank rows (and labels) ------------------------------------
     if (P.tma) {
       if (!staged && warp == 0)
-        if (W == 2 && a.tmap_box)
-          issue_tile_boxes(a, P, s0, ns, stageb, lab_land, &mbar, lane);
+        if (a.tmap_box)
+          issue_tile_boxes(a, P, s0, ns, W, stageb, lab_land, &mbar, lane);
         else
           issue_tile_tma(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane);
     } else {
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const __grid_constant__ Ev
         if (warp == 0) {
           const int64_t xs0 = X.start + xv.tile * (int64_t)S;
           const int64_t xrem = X.start + X.count - xs0;
-          if (W == 2 && a.tmap_box)
-            issue_tile_boxes(a, X, xs0, xrem < S ? (int)xrem : S, stageb, lab_land, &mbar, lane);
+          if (a.tmap_box)
+            issue_tile_boxes(a, X, xs0, xrem < S ? (int)xrem : S, W, stageb, lab_land, &mbar, lane);
           else
             issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, stageb, lab_land,
                          a.lab_stage, &mbar, lane);
@@ -356,10 +356,13 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
       // GB300: 1.5x faster than 8 warps).  Among the shapes that keep two CTAs
       // per SM, take the least estimated makespan: waves of work items (S
       // samples x TG trees) over the resident CTAs, each costing its S TG
-      // evaluations plus a staging overhead worth about 7000 + 170 F evaluations
-      // (tile copies, masks, node tables; fitted to shape sweeps at n = 1e5,
-      // F = 20 and n = 1e7, F = 10).  Few large items leave CTAs idle in the
-      // last wave; many small ones pay the overhead.
+      // evaluations plus a staging overhead worth about 7000 + 170 c
+      // evaluations, c the bulk copies a tile takes (~100 cycles each to issue:
+      // S / 256 tensor boxes for uint16 rows, F for uint32 rows -- their
+      // one-box form for tiles of <= 256 samples measured no faster, as the
+      // smaller tiles pay the rest of the overhead twice), fitted to shape
+      // sweeps at n = 1e5, F = 20 and n = 1e7, F = 10.  Few large items leave
+      // CTAs idle in the last wave; many small ones pay the overhead.
       const int64_t ncta = 2 * (int64_t)ctx->num_sms;
       double best = -1.0;
       for (int S : {2048, 1024, 512, 256})
@@ -368,7 +371,8 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
           if (tg < 16 || eval_smem(mode, W, D, S, tg, F, K, 16) > two_per_sm) continue;
           const int64_t items = work(S, tg);
           const double waves = (double)((items + ncta - 1) / ncta);
-          const double cost = waves * ((double)S * tg + 7000.0 + 170.0 * F);
+          const int copies = (W == 2) ? std::max(1, S / 256) : F;
+          const double cost = waves * ((double)S * tg + 7000.0 + 170.0 * copies);
           if (best < 0 || cost < best) {
             best = cost;
             c.S = S;
@@ -420,10 +424,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// The uint16 rows of a plan as one 2-D tensor map ([F] rows of `ncols` columns,
+// The rank rows of a plan as one 2-D tensor map ([F] rows of `ncols` columns,
 // row stride ld), boxes of BX columns x F rows; false when the plan's problems
-// do not share one TMA-able rank array or the driver declines.
-static bool encode_rank_map(const EvalPlan& plan, int S, EvalArgs* a) {
+// do not share one TMA-able rank array or the driver declines.  uint16 tiles
+// take boxes of 256 (or 128) samples (the re-layout reads them box-major);
+// uint32 tiles route from the landing zone in natural order, so they take one
+// box of the whole tile, which needs S <= 256.
+static bool encode_rank_map(const EvalPlan& plan, int S, int W, EvalArgs* a) {
   const void* base = nullptr;
   int64_t ld = 0, ncols = 0;
   if (plan.d_probs == nullptr) {
@@ -437,16 +444,17 @@ static bool encode_rank_map(const EvalPlan& plan, int S, EvalArgs* a) {
     ld = plan.shared_ld;
     ncols = plan.shared_ncols;
   }
-  const int BX = (S % 256 == 0) ? 256 : 128;
-  if (S % BX != 0 || plan.Fmax < 1 || plan.Fmax > 256 || ncols < 1) return false;
-  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 2) % 16 != 0) return false;
+  const int BX = (W == 4) ? S : ((S % 256 == 0) ? 256 : 128);
+  if (BX > 256 || S % BX != 0 || plan.Fmax < 1 || plan.Fmax > 256 || ncols < 1) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * W) % 16 != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)ncols, (cuuint64_t)plan.Fmax};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * W};
   const cuuint32_t box[2] = {(cuuint32_t)BX, (cuuint32_t)plan.Fmax};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(&a->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = enc(&a->tmap, W == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                   2, const_cast<void*>(base), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return false;
@@ -510,9 +518,10 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
     DEOCT_CUDA_TRY(cudaEventRecord(e0, stream));
   }
   const int Q = ((1 << D) * plan.Kmax + 31) / 32;
-  // uint16 rows on the re-laid kernel: a tile arrives as S / BX 2-D tensor boxes
+  // re-laid kernel: a tile arrives as 2-D tensor boxes (uint16: S / BX boxes;
+  // uint32: one box, tiles of at most 256 samples)
   a.tmap_box = 0;
-  if (W == 2 && !streaming) encode_rank_map(plan, cfg.S, &a);
+  if (!streaming && (W == 2 || cfg.S <= 256)) encode_rank_map(plan, cfg.S, W, &a);
   EvalConfig scfg = cfg;  // the streaming kernel has a producer warp and >= 1 routing warp
   if (scfg.warps < 2) scfg.warps = 2;
   int rc = streaming ? launch_stream(ctx, W, D, Q, a, scfg, smem, stream)

@@ -42,7 +42,7 @@ constexpr int kQMax = 4;       // ballot mode: up to 4 bins per lane (2^D * K <=
 constexpr int kMaxStages = 3;  // streaming kernel: landing zones per CTA
 
 struct EvalArgs {
-  // uint16 rows of every problem as one 2-D TMA tensor ([F] rows x width
+  // the rank rows of every problem as one 2-D TMA tensor ([F] rows x width
   // columns, boxes of tmap_box columns x F rows), valid when tmap_box > 0
   CUtensorMap tmap;
   int tmap_box;
@@ -392,24 +392,25 @@ __device__ __forceinline__ void issue_tile_tma(const EvalProb& P, int64_t s0, in
   }
 }
 
-// Stage a tile through the tensor map (uint16 rows): boxes of tmap_box samples
-// x F rows land box-major -- box b at dst + b Fmax tmap_box 2 bytes, row f of a
-// box at f tmap_box 2 bytes -- one 2-D copy per box; the labels by one 1-D
-// copy.  Called by all lanes of one warp.
+// Stage a tile through the tensor map: boxes of tmap_box samples x F rows land
+// box-major -- box b at dst + b Fmax tmap_box W bytes, row f of a box at
+// f tmap_box W bytes (one box of the whole tile is the natural [F][S] order) --
+// one 2-D copy per box; the labels by one 1-D copy.  Called by all lanes of
+// one warp.
 __device__ __forceinline__ void issue_tile_boxes(const EvalArgs& a, const EvalProb& P, int64_t s0,
-                                                 int ns, unsigned char* dst, unsigned char* labdst,
-                                                 uint64_t* bar, int lane) {
+                                                 int ns, int W, unsigned char* dst,
+                                                 unsigned char* labdst, uint64_t* bar, int lane) {
   fence_proxy_async_smem();
   const int BX = a.tmap_box;
   const int nbox = (ns + BX - 1) / BX;
-  const uint32_t boxbytes = (uint32_t)BX * (uint32_t)P.F * 2u;
+  const uint32_t boxbytes = (uint32_t)BX * (uint32_t)P.F * (uint32_t)W;
   const uint32_t lbytes = (uint32_t)tma_label_bytes(P, ns, a.lab_stage);
   if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)nbox * boxbytes + lbytes);
   __syncwarp();
   const int ncopy = nbox + (lbytes ? 1 : 0);
   for (int c = lane; c < ncopy; c += 32) {
     if (c < nbox)
-      bulk_tensor_2d_g2s(dst + (size_t)c * a.Fmax * BX * 2, &a.tmap, (int)(s0 + (int64_t)c * BX), 0, bar);
+      bulk_tensor_2d_g2s(dst + (size_t)c * a.Fmax * BX * W, &a.tmap, (int)(s0 + (int64_t)c * BX), 0, bar);
     else
       bulk_g2s(labdst, P.labels + s0, lbytes, bar);
   }
