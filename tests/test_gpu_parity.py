@@ -499,3 +499,26 @@ def test_encode_and_eval_at_max_samples(c):
     _, ref_err, _, _ = oracle.fitness(ref, a, n)
     np.testing.assert_array_equal(u32(counts), ref)
     np.testing.assert_array_equal(u32(errors), ref_err)
+
+
+def test_deoct_workload0_matches_golden_fixture(c):
+    """The GPU DEOCT fit of the tiny workload reproduces the stored fixture of
+    tests/golden/deoct_workload0.json (written from the oracle alone): the best tree, its
+    fitness, and the final population bit for bit."""
+    import hashlib
+    import json
+    import os
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "deoct_workload0.json")) as f:
+        gold = json.load(f)
+    w = datagen.make_workload(0)
+    ds = gpu_dataset(c, w["X"], w["y"], w["K"], 2)
+    prm = deoct.make_params(w["depth"], w["P"], w["G"], mut_f=w["M"], cr=w["CR"], seed=w["seed"])
+    B = (1 << w["depth"]) - 1
+    pop = torch.empty((w["P"], 2 * B), dtype=torch.float32, device="cuda")
+    a, th, fit = deoct.deoct_fit_subtree(c, ds, prm, stream_id=0, pop_out=pop)
+    assert [int(x) for x in a] == gold["best_tree_a"]
+    assert [int(x) for x in th] == gold["best_tree_theta"]
+    assert fit == gold["best_fitness_per_generation"][-1]
+    assert hashlib.sha256(pop.cpu().numpy().tobytes()).hexdigest() == gold["final_population_sha256"]

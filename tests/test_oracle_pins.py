@@ -572,3 +572,21 @@ def test_deoct_warm_start_bounds_the_root():
     f, _, _, _ = oracle.fitness(counts, sub_a, 400)
     out = oracle.mh(ranks, nu, w["y"], 2, depth=3, horizon=2, P=8, G=0, seed=2, de_seeds=True)
     assert out["kind"][0] == 2 and out["node_fit"][0] <= f[0]
+
+
+def test_oracle_reproduces_golden_fixtures():
+    """tests/golden/ holds values written by tests/golden/make_golden.py from the oracle alone
+    (the paper prints no worked numeric example): DEOCT on the tiny workload (Algorithm 4) and
+    the class counts of the full population-evaluation workload (Algorithm 1).  The oracle must
+    still produce them; a change here needs a change of the oracle's arithmetic that a passage of
+    the paper justifies."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    for name, fn in (("deoct_workload0.json", mg.deoct_workload0), ("eval_workload1.json", mg.eval_workload1)):
+        with open(os.path.join(here, name)) as f:
+            assert fn() == json.load(f), name
