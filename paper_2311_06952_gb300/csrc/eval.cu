@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(512, 2) eval_kernel(const __grid_constant__ Ev
     // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
     const int lab_done = tma_label_bytes(P, ns, a.lab_stage);
     if (MODE == 0) {
-      class_masks<Q>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, nw, aux32);
+      class_masks<Q, PairGeom<W, false>::kShared>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane,
+                                                  warp, nw, aux32);
     } else {
       for (int j = threadIdx.x; j < 2 * npair * 32; j += blockDim.x)
         lab_s[j] = (uint8_t)tile_label(P, lab_land, lab_done, s0, j, ns);

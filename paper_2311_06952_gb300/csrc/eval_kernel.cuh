@@ -21,6 +21,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -171,11 +172,16 @@ __device__ __forceinline__ uint32_t tile_offset(uint32_t j) {
 // Where lane l finds the two samples of chunk pair p: at p * kPairStride +
 // l * kLane and kSecond bytes further.  NAT: natural sample order (streaming
 // kernel; uint16 lanes then pair up on 32-bit words, at most 2-way conflicts).
+// kShared: the re-laid uint16 tile, where the pair's two samples of a row
+// share one 32-bit word (the root is then read once for both chunks, the class
+// masks of the pair sit side by side, and with one bin per lane the pair loop
+// is unrolled by two).
 template <int W, bool NAT>
 struct PairGeom {
   static constexpr uint32_t kSecond = (W == 4) ? 128u : (NAT ? 64u : 2u);
   static constexpr uint32_t kPairStride = 64u * W;
   static constexpr uint32_t kLane = (W == 2 && NAT) ? 2u : 4u;
+  static constexpr bool kShared = (W == 2 && !NAT);
 };
 
 template <int W>
@@ -220,7 +226,9 @@ __device__ __forceinline__ int bar_or_n(int n, int pred) {
 // Route 64 samples (the two chunks of pair p) of one tree and add the bin
 // counts owned by this lane.  Ballot of level d = "went right" at depth d for
 // the 32 samples of a chunk; bin b = leaf*K + k is owned by lane b % 32.
-template <int W, int D, int Q, bool NAT>
+// R32 (shared-word tiles, root theta <= 0xFFFF): one 32-bit load gives both
+// chunks' root ranks, and th0 arrives shifted to the high half.
+template <int W, int D, int Q, bool NAT, bool R32>
 __device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
                                            uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
                                            uint32_t tnb48, uint32_t ntnb, uint32_t ymA, uint32_t ymB,
@@ -228,9 +236,19 @@ __device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t 
   constexpr uint32_t SEC = PairGeom<W, NAT>::kSecond;
   uint32_t BA[D], BB[D];
   // level 0: the root is the same node for every lane
-  const uint32_t ra0 = lds_rank<W>(row0 + jb);
-  const uint32_t rb0 = lds_rank<W>(row0 + jb + SEC);
-  const bool pa0 = ra0 >= th0, pb0 = rb0 >= th0;
+  bool pa0, pb0;
+  if constexpr (R32) {
+    // word = A | B << 16: B >= th <=> word >= th << 16, and A likewise
+    // after shifting A into the high half
+    const uint32_t w0 = lds_u32(row0 + jb);
+    pa0 = (w0 << 16) >= th0;
+    pb0 = w0 >= th0;
+  } else {
+    const uint32_t ra0 = lds_rank<W>(row0 + jb);
+    const uint32_t rb0 = lds_rank<W>(row0 + jb + SEC);
+    pa0 = ra0 >= th0;
+    pb0 = rb0 >= th0;
+  }
   BA[0] = __ballot_sync(0xFFFFFFFFu, pa0);
   BB[0] = __ballot_sync(0xFFFFFFFFu, pb0);
   if (D >= 2) {
@@ -262,8 +280,15 @@ __device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t 
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    uint32_t ma = lds_u32(ymA + q * 128u);
-    uint32_t mb = lds_u32(ymB + q * 128u);
+    uint32_t ma, mb;
+    if constexpr (PairGeom<W, NAT>::kShared) {  // [pair][q][lane][chunk]
+      const uint2 m2 = lds_node(ymA + q * 256u);
+      ma = m2.x;
+      mb = m2.y;
+    } else {  // [chunk][q][lane]
+      ma = lds_u32(ymA + q * 128u);
+      mb = lds_u32(ymB + q * 128u);
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       ma &= BA[d] ^ cst[q][d];
@@ -296,12 +321,38 @@ __device__ __forceinline__ void route_group(int nt, int npair, uint32_t jb0, con
 #pragma unroll
     for (int q = 0; q < Q; ++q) cnt[q] = 0u;
     const uint32_t ntnb = 0u - tnb;
-    for (int pp = sl; pp < npair; pp += step) {
-      const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
-      const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
-      const uint32_t ymB = ymA + Q * 128u;
-      route_pair<W, D, Q, NAT>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u, tnb + 48u, ntnb,
-                               ymA, ymB, cst, cnt);
+    if constexpr (G::kShared) {
+      auto one = [&](int pp, auto r32) {
+        constexpr bool R32 = decltype(r32)::value;
+        const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
+        const uint32_t ym = aux_sa + ((uint32_t)pp * Q * 64u + (uint32_t)lane * 2u) * 4u;
+        route_pair<W, D, Q, NAT, R32>(jb, n1.x, R32 ? (n1.y << 16) : n1.y, n2.x, n2.y, n3.x, n3.y,
+                                      tnb + 32u, tnb + 48u, ntnb, ym, ym, cst, cnt);
+      };
+      auto walk = [&](auto r32) {
+        int pp = sl;
+        if constexpr (Q == 1) {  // by two (more bins per lane would spill)
+          for (; pp + step < npair; pp += 2 * step) {
+            one(pp, r32);
+            one(pp + step, r32);
+          }
+          if (pp < npair) one(pp, r32);
+        } else {
+          for (; pp < npair; pp += step) one(pp, r32);
+        }
+      };
+      if (n1.y <= 0xFFFFu)
+        walk(std::true_type{});
+      else
+        walk(std::false_type{});
+    } else {
+      for (int pp = sl; pp < npair; pp += step) {
+        const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
+        const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
+        const uint32_t ymB = ymA + Q * 128u;
+        route_pair<W, D, Q, NAT, false>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u,
+                                        tnb + 48u, ntnb, ymA, ymB, cst, cnt);
+      }
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -427,9 +478,10 @@ __device__ __forceinline__ uint32_t tile_label(const EvalProb& P, const uint8_t*
   return P.labels[col];
 }
 
-// Ballot mode: the class masks of the tile's chunks, [chunk][q][lane] -- lane
-// l's word q is the ballot of "label == class of bin l + 32 q".
-template <int Q>
+// Ballot mode: the class masks of the tile's chunks -- lane l's word q is the
+// ballot of "label == class of bin l + 32 q" -- laid out [chunk][q][lane], or
+// with PAIRED [pair][q][lane][chunk] (the two chunks of a pair side by side).
+template <int Q, bool PAIRED>
 __device__ __forceinline__ void class_masks(const EvalProb& P, const uint8_t* lab_land, int lab_done,
                                             int64_t s0, int ns, int npair, int K, int LK, int lane,
                                             int warp, int nw, uint32_t* aux32) {
@@ -451,7 +503,12 @@ __device__ __forceinline__ void class_masks(const EvalProb& P, const uint8_t* la
         if (kq[q] == k) mine[q] = m;
     }
 #pragma unroll
-    for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+    for (int q = 0; q < Q; ++q) {
+      if (PAIRED)
+        aux32[((c >> 1) * Q + q) * 64 + lane * 2 + (c & 1)] = mine[q];
+      else
+        aux32[(c * Q + q) * 32 + lane] = mine[q];
+    }
   }
 }
 

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
           }
         }
       }
-      class_masks<Q>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, ncw, aux32);
+      class_masks<Q, false>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, ncw, aux32);
       bar_sync_n(nct);
       route_group<W, D, Q, true>(jv.ntrees, npair, (uint32_t)z * (uint32_t)lay.sbytes, nodes_s,
                                  nodes_sa, aux_sa, cst, cnt_s, LK, lane, warp, ncw);
