@@ -44,11 +44,11 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
 # kernel source it was taken on: a hash of the re-laid evaluator kernel's text in
 # csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "0d7718b704beb837", "bytes": 366_826_496 + 3_871_744,
+EVAL_TRAFFIC = {"source_sha256_16": "7bfa9057e96f5371", "bytes": 363_230_976 + 3_342_848,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
-                "ncu": {"inst_per_cycle": 3.237, "issue_frac": 3.237 / 4.0, "alu_pipe_frac": 0.7386,
-                        "shared_pipe_frac": 0.816, "inst_per_chunk": 36.35, "dram_gbs": 32.3,
-                        "dram_frac_of_peak": 0.0041}}
+                "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
+                        "shared_pipe_frac": 0.811, "inst_per_chunk": 35.46, "dram_gbs": 33.7,
+                        "dram_frac_of_peak": 0.0050}}
 
 
 def _eval_source_hash():
