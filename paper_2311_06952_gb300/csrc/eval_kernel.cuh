@@ -139,7 +139,8 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(int mode, int W, int 
 // Shared-memory layout of the streaming kernel (ballot mode only):
 //   stage s  [F][S] ranks (natural order), then [S] labels: landing zone s of
 //            the ring, at s * sbytes
-//   nodes, aux (class masks [S/32][Q][32]), cnt as above
+//   nodes, aux (class masks [S/32][Q][32]; the rows of a chunk pair belong to
+//   the one routing warp that owns the pair), cnt as above
 struct StreamLayout {
   size_t rbytes, sbytes, nodes, aux, cnt, total;
 };
@@ -223,18 +224,16 @@ __device__ __forceinline__ int bar_or_n(int n, int pred) {
   return r;
 }
 
-// Route 64 samples (the two chunks of pair p) of one tree and add the bin
-// counts owned by this lane.  Ballot of level d = "went right" at depth d for
-// the 32 samples of a chunk; bin b = leaf*K + k is owned by lane b % 32.
+// The D level ballots of 64 samples (the two chunks of pair p) of one tree:
+// BA[d] / BB[d] = "went right" at depth d for the 32 samples of chunk A / B.
 // R32 (shared-word tiles, root theta <= 0xFFFF): one 32-bit load gives both
 // chunks' root ranks, and th0 arrives shifted to the high half.
-template <int W, int D, int Q, bool NAT, bool R32>
-__device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
-                                           uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
-                                           uint32_t tnb48, uint32_t ntnb, uint32_t ymA, uint32_t ymB,
-                                           const uint32_t (&cst)[Q][D], uint32_t (&cnt)[Q]) {
+template <int W, int D, bool NAT, bool R32>
+__device__ __forceinline__ void route_levels(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
+                                             uint32_t th2, uint32_t row3, uint32_t th3,
+                                             uint32_t tnb32, uint32_t tnb48, uint32_t ntnb,
+                                             uint32_t (&BA)[D], uint32_t (&BB)[D]) {
   constexpr uint32_t SEC = PairGeom<W, NAT>::kSecond;
-  uint32_t BA[D], BB[D];
   // level 0: the root is the same node for every lane
   bool pa0, pb0;
   if constexpr (R32) {
@@ -278,6 +277,18 @@ __device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t 
       }
     }
   }
+}
+
+// Route 64 samples (the two chunks of pair p) of one tree and add the bin
+// counts owned by this lane: bin b = leaf*K + k is owned by lane b % 32, and
+// its count grows by popc(Y_k & AND_d (B_d or ~B_d)).
+template <int W, int D, int Q, bool NAT, bool R32>
+__device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
+                                           uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
+                                           uint32_t tnb48, uint32_t ntnb, uint32_t ymA, uint32_t ymB,
+                                           const uint32_t (&cst)[Q][D], uint32_t (&cnt)[Q]) {
+  uint32_t BA[D], BB[D];
+  route_levels<W, D, NAT, R32>(jb, row0, th0, row2, th2, row3, th3, tnb32, tnb48, ntnb, BA, BB);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     uint32_t ma, mb;

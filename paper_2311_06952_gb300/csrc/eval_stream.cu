@@ -4,31 +4,107 @@
 // Warp-specialised: the last warp of the CTA stages tiles into a ring of
 // `nstage` landing zones (rank rows + labels, 1-D bulk copies), the other warps
 // route.  Each zone has a `full` mbarrier (the copies landed, or a plain
-// arrival when the consumers must gather the tile themselves) and an `empty`
-// one (the consumers are done with it).  Issuing a bulk copy costs the issuing
-// warp ~100 cycles per copy (measured on GB300), which the producer warp
-// spends off the routing warps' critical path; with two or three zones the
-// copies of later tiles are in flight while a tile is routed.  Trees route
-// straight from the landing zone in the natural sample order the copies write
-// (no re-layout pass).  This is the kernel for groups of fewer than 16 trees,
-// where HBM, not routing, sets the pace.
+// arrival when the routing warps must gather the tile themselves) and an
+// `empty` one that every routing warp arrives on once it is done with the
+// zone.  Issuing a bulk copy costs the issuing warp ~100 cycles per copy
+// (measured on GB300), which the producer warp spends off the routing warps'
+// critical path; with two or three zones the copies of later tiles are in
+// flight while a tile is routed.
+//
+// Each routing warp waits for the zone itself and releases it with its own
+// arrival.  For groups of one to three trees the routing warps do not meet per
+// tile at all: each owns the same chunk pairs of every tile (for every tree of
+// the job) and computes the class masks of its own pairs.  Larger groups share
+// the tile's class masks (two barriers per tile).  Job changes and gathered
+// (subset-index) tiles also meet; every routing warp reaches each of these
+// barriers at the same tile.  Trees route straight from the landing zone in the
+// natural sample order the copies write (no re-layout pass).  This is the
+// kernel for groups of fewer than 16 trees, where HBM, not routing, sets the
+// pace.
 #include "eval_kernel.cuh"
 
 namespace deoct {
 namespace evk {
 namespace {
 
+// Groups of fewer trees than this route pair-sliced (every warp its own chunk
+// pairs of every tree, no CTA barrier per tile); larger groups share the
+// tile's class masks and split trees over warps, with two barriers per tile
+// (measured: pair slicing is 10% faster for one tree, 5% for two, even at four
+// and 11% slower at eight).
+constexpr int kPairSliceTrees = 4;
+
+// One routing warp's share of a tile: chunk pairs warp, warp + ncw, ... of
+// every tree of the job.  The warp first writes the class masks of its pairs
+// ([chunk][q][lane]: lane l's word q is the ballot of "label == class of bin
+// l + 32 q") to rows of `aux` that no other warp touches, then routes each tree
+// over its pairs from the landing zone and adds the bin counts to the job's
+// shared counts with one atomic per (tree, bin) per tile.  jb0: byte offset of
+// the zone from the row addresses held in the node table.
+template <int W, int D, int Q>
+__device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair, uint32_t jb0,
+                                            const uint2* nodes_s, uint32_t nodes_sa,
+                                            uint32_t* aux32, uint32_t aux_sa,
+                                            const uint8_t* lab_land, int lab_done, int64_t s0,
+                                            int ns, int K, const int (&kq)[Q],
+                                            const uint32_t (&cst)[Q][D], uint32_t* cnt_s, int LK,
+                                            int lane, int warp, int ncw) {
+  constexpr int B = (1 << D) - 1;
+  typedef PairGeom<W, true> G;
+  if (warp >= npair) return;
+  for (int c = 2 * warp; c < 2 * npair; c += (c & 1) ? 2 * ncw - 1 : 1) {
+    const uint32_t y = tile_label(P, lab_land, lab_done, s0, c * 32 + lane, ns);
+    uint32_t mine[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) mine[q] = 0u;
+    for (int k = 0; k < K; ++k) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, y == (uint32_t)k);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (kq[q] == k) mine[q] = m;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+  }
+  __syncwarp();
+  for (int i = 0; i < nt; ++i) {
+    const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
+    const uint2 n1 = nodes_s[i * B];
+    uint2 n2 = n1, n3 = n1;
+    if (D >= 2) {
+      n2 = nodes_s[i * B + 1];
+      n3 = nodes_s[i * B + 2];
+    }
+    const uint32_t ntnb = 0u - tnb;
+    uint32_t cnt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cnt[q] = 0u;
+    for (int pp = warp; pp < npair; pp += ncw) {
+      const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
+      const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
+      const uint32_t ymB = ymA + Q * 128u;
+      route_pair<W, D, Q, true, false>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u,
+                                       tnb + 48u, ntnb, ymA, ymB, cst, cnt);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int b = lane + 32 * q;
+      if (b < LK) atomicAdd(&cnt_s[i * LK + b], cnt[q]);
+    }
+  }
+}
+
 template <int W, int D, int Q>
 __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_constant__ EvalArgs a) {
   typedef typename RankT<W>::T RT;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
-  __shared__ uint8_t s_kind[kMaxStages];  // 1: zone's tile by bulk copy; 0: consumers gather it
+  __shared__ volatile int s_abort;  // a routing warp's bounded wait ran out
 
   const int S = a.S, NS = a.nstage;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps; warp ncw stages
+  const int ncw = (int)(blockDim.x >> 5) - 1;  // routing warps; warp ncw stages
   const int nct = ncw * 32;
   const StreamLayout lay = stream_layout(W, D, S, a.TG, a.Fmax, a.Kmax, NS, a.lab_stage);
   uint2* nodes_s = reinterpret_cast<uint2*>(smem + lay.nodes);
@@ -45,9 +121,10 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
   if (threadIdx.x == 0) {
     for (int z = 0; z < NS; ++z) {
       mbar_init(&full[z], 1);
-      mbar_init(&empty[z], 1);
+      mbar_init(&empty[z], (uint32_t)ncw);
     }
     fence_mbar_init();
+    s_abort = 0;
   }
   __syncthreads();
 
@@ -76,15 +153,12 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
       const EvalProb& X = *pv.p;
       unsigned char* zone = smem + (size_t)z * lay.sbytes;
       if (X.tma) {
-        if (lane == 0) s_kind[z] = 1;
-        __syncwarp();
         const int64_t xs0 = X.start + pv.tile * (int64_t)S;
         const int64_t xrem = X.start + X.count - xs0;
         issue_tile_tma(X, xs0, xrem < S ? (int)xrem : S, S, W, zone, zone + lay.rbytes,
                        a.lab_stage, &full[z], lane);
       } else if (lane == 0) {
-        s_kind[z] = 0;
-        mbar_arrive(&full[z]);
+        mbar_arrive(&full[z]);  // the routing warps gather this tile themselves
       }
       issued |= 1u << z;
       __syncwarp();
@@ -103,11 +177,13 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
           mbar_wait_bounded(&full[q], r & 1u, a.status);
         }
   } else {
-    // ---- consumers: route tile t0 + i from zone i % NS ---------------------
+    // ---- routing warps: their share of tile t0 + i from zone i % NS --------
     uint32_t cst[Q][D];  // per owned bin, "right" (0) or "left" (~0) at level d
+    int kq[Q];           // class of each owned bin (-1: none)
     int K = 0;
-    int z = 0;        // zone of tile gt: (gt - t0) % NS
-    uint32_t ph = 0;  // parity of its phase: ((gt - t0) / NS) & 1
+    int z = 0;          // zone of tile gt: (gt - t0) % NS
+    uint32_t ph = 0;    // parity of its phase: ((gt - t0) / NS) & 1
+    bool dead = false;  // a bounded wait ran out: skip the work, keep the barriers
     for (int64_t gt = t0; gt < t1; ++gt) {
       JobView nv;  // job and tile of gt: a search at the first tile, then a step
       if (gt == t0) {
@@ -117,53 +193,81 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
         advance_job(a, gt, &nv);
       }
       if (nv.job != cur_job) {
+        bar_sync_n(nct);  // every routing warp is done with the previous job
         if (cur_job >= 0) flush_job(jv, cnt_s, LK, nct);
-        bar_sync_n(nct);
+        bar_sync_n(nct);  // its counts are read before the new job zeroes them
         jv = nv;
         cur_job = nv.job;
         setup_job<D, Q, true>(jv, nodes_s, cnt_s, stage0_sa, S, W, a.status, lane, nct, cst, &K, &LK);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int b = lane + 32 * q;
+          kq[q] = (b < LK) ? b % K : -1;
+        }
+        bar_sync_n(nct);  // node table and zeroed counts visible to every warp
       }
       jv.tile = nv.tile;
       const EvalProb& P = *jv.p;
       const int64_t s0 = P.start + jv.tile * (int64_t)S;
       const int64_t rem = P.start + P.count - s0;
       const int ns = rem < S ? (int)rem : S;
-      const int nch = (ns + 31) >> 5;
-      const int npair = (nch + 1) >> 1;
+      const int npair = (((ns + 31) >> 5) + 1) >> 1;
       unsigned char* zone = smem + (size_t)z * lay.sbytes;
       const uint8_t* lab_land = zone + lay.rbytes;
 
-      // one thread polls the zone's mbarrier while the others sleep in the
-      // consumers' barrier; each then acquires the zone through the completed
-      // phase (the test succeeds at once)
-      int ok = 1;
-      if (threadIdx.x == 0) ok = mbar_wait_bounded(&full[z], ph, a.status) ? 1 : 0;
-      if (bar_or_n(nct, !ok)) break;  // timed out (status recorded)
-      if (threadIdx.x != 0) mbar_try_wait(&full[z], ph);
-      int lab_done = 0;
-      if (s_kind[z]) {
-        lab_done = tma_label_bytes(P, ns, a.lab_stage);
-      } else {
-        // gathered subset or unaligned rows: plain loads in natural order
-        const RT* src = static_cast<const RT*>(P.ranks);
-        for (int e = threadIdx.x; e < P.F * S; e += nct) {
-          int f = e / S, j = e - f * S;
-          if (j < ns) {
-            int64_t col = P.idx ? (int64_t)P.idx[s0 + j] : s0 + j;
-            if ((uint64_t)col >= (uint64_t)P.ncols) {
-              atomicOr(a.status, ST_BAD_INDEX);
-              col = 0;
-            }
-            reinterpret_cast<RT*>(zone + (size_t)f * S * W)[j] = src[(int64_t)f * P.ld + col];
-          }
+      // lane 0 polls the zone's mbarrier; then every lane acquires the zone
+      // through the completed phase (the test succeeds at once)
+      if (!dead && s_abort) dead = true;
+      if (!dead) {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&full[z], ph, a.status) ? 1 : 0;
+        if (__shfl_sync(0xFFFFFFFFu, ok, 0)) {
+          mbar_try_wait(&full[z], ph);
+        } else {  // timed out (status recorded)
+          dead = true;
+          if (lane == 0) s_abort = 1;
         }
       }
-      class_masks<Q, false>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, ncw, aux32);
-      bar_sync_n(nct);
-      route_group<W, D, Q, true>(jv.ntrees, npair, (uint32_t)z * (uint32_t)lay.sbytes, nodes_s,
-                                 nodes_sa, aux_sa, cst, cnt_s, LK, lane, warp, ncw);
-      bar_sync_n(nct);
-      if (threadIdx.x == 0) mbar_arrive(&empty[z]);  // the producer may restage zone z
+      int lab_done = 0;
+      if (P.tma) {
+        lab_done = tma_label_bytes(P, ns, a.lab_stage);
+      } else {
+        // gathered subset or unaligned rows: the routing warps gather the
+        // tile with plain loads in natural order, then meet
+        if (!dead) {
+          const RT* src = static_cast<const RT*>(P.ranks);
+          for (int e = threadIdx.x; e < P.F * S; e += nct) {
+            int f = e / S, jj = e - f * S;
+            if (jj < ns) {
+              int64_t col = P.idx ? (int64_t)P.idx[s0 + jj] : s0 + jj;
+              if ((uint64_t)col >= (uint64_t)P.ncols) {
+                atomicOr(a.status, ST_BAD_INDEX);
+                col = 0;
+              }
+              reinterpret_cast<RT*>(zone + (size_t)f * S * W)[jj] = src[(int64_t)f * P.ld + col];
+            }
+          }
+        }
+        bar_sync_n(nct);
+      }
+      const uint32_t jb0 = (uint32_t)z * (uint32_t)lay.sbytes;
+      if (jv.ntrees < kPairSliceTrees) {
+        if (!dead)
+          route_share<W, D, Q>(P, jv.ntrees, npair, jb0, nodes_s, nodes_sa, aux32, aux_sa, lab_land,
+                               lab_done, s0, ns, K, kq, cst, cnt_s, LK, lane, warp, ncw);
+      } else {
+        // larger groups: the tile's class masks once, shared by every warp
+        if (!dead)
+          class_masks<Q, false>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, ncw,
+                                aux32);
+        bar_sync_n(nct);
+        if (!dead)
+          route_group<W, D, Q, true>(jv.ntrees, npair, jb0, nodes_s, nodes_sa, aux_sa, cst, cnt_s,
+                                     LK, lane, warp, ncw);
+        bar_sync_n(nct);  // no warp rewrites the masks while another still reads them
+      }
+      __syncwarp();
+      if (!dead && lane == 0) mbar_arrive(&empty[z]);  // this warp is done with zone z
       if (++z == NS) {
         z = 0;
         ph ^= 1u;
