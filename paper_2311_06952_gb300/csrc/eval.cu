@@ -345,12 +345,15 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
     c.warps = 16;
     if (P < 16) {
       // small groups run on the streaming kernel, where (measured on GB300,
-      // n = 1e7, P = 1..8) tiles of 1024 samples and 9 warps -- 8 routing warps
-      // and the producer -- keep the most tiles in flight per SM
+      // n = 1e7, P = 1..12) 9 warps -- 8 routing warps and the producer -- and
+      // tiles of 2048 samples (pair-sliced groups: a ring of two landing zones)
+      // or 1024 (three zones) do best, at two or more CTAs per SM
       c.TG = P;
-      c.S = 1024;
+      const bool sliced = P < kPairSliceTrees;
+      c.S = sliced ? 2048 : 1024;
       c.warps = 9;
-      while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps) > two_per_sm && c.S > 256) c.S /= 2;
+      while (eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps, sliced ? 2 : 0) > two_per_sm && c.S > 256)
+        c.S /= 2;
       while (work(c.S, c.TG) < 2 * (int64_t)ctx->num_sms && c.S > 256) c.S /= 2;
     } else {
       // A warp owns a tree; 16 warps per CTA and two CTAs per SM (measured on

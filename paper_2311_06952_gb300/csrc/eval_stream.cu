@@ -27,13 +27,6 @@ namespace deoct {
 namespace evk {
 namespace {
 
-// Groups of fewer trees than this route pair-sliced (every warp its own chunk
-// pairs of every tree, no CTA barrier per tile); larger groups share the
-// tile's class masks and split trees over warps, with two barriers per tile
-// (measured: pair slicing is 10% faster for one tree, 5% for two, even at four
-// and 11% slower at eight).
-constexpr int kPairSliceTrees = 4;
-
 // One routing warp's share of a tile: chunk pairs warp, warp + ncw, ... of
 // every tree of the job.  The warp first writes the class masks of its pairs
 // ([chunk][q][lane]: lane l's word q is the ballot of "label == class of bin
@@ -52,19 +45,37 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
   constexpr int B = (1 << D) - 1;
   typedef PairGeom<W, true> G;
   if (warp >= npair) return;
-  for (int c = 2 * warp; c < 2 * npair; c += (c & 1) ? 2 * ncw - 1 : 1) {
-    const uint32_t y = tile_label(P, lab_land, lab_done, s0, c * 32 + lane, ns);
-    uint32_t mine[Q];
+  if (K == 2 && lab_done >= 64 * npair) {
+    // two classes, every label of the tile landed: all bins of a lane have
+    // class lane % 2 (bin lane + 32 q), so one pair of ballots serves them
+    const bool odd = lane & 1;
+    for (int pp = warp; pp < npair; pp += ncw) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) mine[q] = 0u;
-    for (int k = 0; k < K; ++k) {
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, y == (uint32_t)k);
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * pp + h;
+        const uint32_t y = lab_land[c * 32 + lane];
+        const uint32_t y1 = __ballot_sync(0xFFFFFFFFu, y == 1u);
+        const uint32_t y0 = __ballot_sync(0xFFFFFFFFu, y == 0u);
+        const uint32_t m = odd ? y1 : y0;
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (kq[q] == k) mine[q] = m;
+        for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = kq[q] >= 0 ? m : 0u;
+      }
     }
+  } else {
+    for (int c = 2 * warp; c < 2 * npair; c += (c & 1) ? 2 * ncw - 1 : 1) {
+      const uint32_t y = tile_label(P, lab_land, lab_done, s0, c * 32 + lane, ns);
+      uint32_t mine[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+      for (int q = 0; q < Q; ++q) mine[q] = 0u;
+      for (int k = 0; k < K; ++k) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, y == (uint32_t)k);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (kq[q] == k) mine[q] = m;
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+    }
   }
   __syncwarp();
   for (int i = 0; i < nt; ++i) {

@@ -399,13 +399,14 @@ def test_eval_is_one_launch_and_leaves_no_state(c, lab_off):
     np.testing.assert_array_equal(u32(errors), ref_err)
 
 
-@pytest.mark.parametrize("depth,K", [(4, 2), (3, 5), (5, 3)])
+@pytest.mark.parametrize("depth,K", [(4, 2), (5, 2), (3, 5), (5, 3)])
 @pytest.mark.parametrize("rb", [2, 4])
 def test_eval_small_groups_streaming_bit_exact(c, depth, K, rb):
     """Groups of fewer than 16 trees run on the streaming kernel (a producer warp keeps a ring of
     landing zones filled; routing warps read the natural sample order).  P = 1, 2, 5, 15 on all
     samples and on a gathered subset; the default grid (about one tile per CTA here) and a grid
-    of 7 CTAs that cycles each ring many times; 1, 2 and 3 bins per lane; a ragged tail."""
+    of 7 CTAs that cycles each ring many times; 1, 2 and 3 bins per lane; two classes (whose
+    masks take a shortcut when every label of a tile has landed) and more; a ragged tail."""
     from paper_2311_06952_gb300 import deoct
     rng = _rng(900 + 10 * depth + K + rb)
     n, F = 200_003, 7
