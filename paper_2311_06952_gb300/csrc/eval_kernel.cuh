@@ -500,7 +500,10 @@ __device__ __forceinline__ uint32_t tile_label(const EvalProb& P, const uint8_t*
 // Ballot mode: the class masks of the tile's chunks -- lane l's word q is the
 // ballot of "label == class of bin l + 32 q" -- laid out [chunk][q][lane], or
 // with PAIRED [pair][q][lane][chunk] (the two chunks of a pair side by side).
-template <int Q, bool PAIRED>
+// EVENODD: chunk 2p holds the even and chunk 2p + 1 the odd samples of the
+// 64-sample block p (lane l: samples 64p + 2l and 64p + 2l + 1), else chunk c
+// holds samples 32c .. 32c + 31.
+template <int Q, bool PAIRED, bool EVENODD = false>
 __device__ __forceinline__ void class_masks(const EvalProb& P, const uint8_t* lab_land, int lab_done,
                                             int64_t s0, int ns, int npair, int K, int LK, int lane,
                                             int warp, int nw, uint32_t* aux32) {
@@ -511,7 +514,8 @@ __device__ __forceinline__ void class_masks(const EvalProb& P, const uint8_t* la
     kq[q] = (b < LK) ? b % K : -1;
   }
   for (int c = warp; c < 2 * npair; c += nw) {
-    const uint32_t y = tile_label(P, lab_land, lab_done, s0, c * 32 + lane, ns);
+    const int j = EVENODD ? 64 * (c >> 1) + 2 * lane + (c & 1) : c * 32 + lane;
+    const uint32_t y = tile_label(P, lab_land, lab_done, s0, j, ns);
     uint32_t mine[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) mine[q] = 0u;

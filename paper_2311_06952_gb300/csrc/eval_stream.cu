@@ -18,9 +18,10 @@
 // the tile's class masks (two barriers per tile).  Job changes and gathered
 // (subset-index) tiles also meet; every routing warp reaches each of these
 // barriers at the same tile.  Trees route straight from the landing zone in the
-// natural sample order the copies write (no re-layout pass).  This is the
-// kernel for groups of fewer than 16 trees, where HBM, not routing, sets the
-// pace.
+// natural sample order the copies write (no re-layout pass; uint16 chunks take
+// the even and the odd samples of a 64-sample block, so a pair's two samples
+// of a row share one word).  This is the kernel for groups of fewer than 16
+// trees, where HBM, not routing, sets the pace.
 #include "eval_kernel.cuh"
 
 namespace deoct {
@@ -28,12 +29,17 @@ namespace evk {
 namespace {
 
 // One routing warp's share of a tile: chunk pairs warp, warp + ncw, ... of
-// every tree of the job.  The warp first writes the class masks of its pairs
-// ([chunk][q][lane]: lane l's word q is the ballot of "label == class of bin
-// l + 32 q") to rows of `aux` that no other warp touches, then routes each tree
-// over its pairs from the landing zone and adds the bin counts to the job's
-// shared counts with one atomic per (tree, bin) per tile.  jb0: byte offset of
-// the zone from the row addresses held in the node table.
+// every tree of the job.  The warp first writes the class masks of its pairs to
+// entries of `aux` that no other warp touches, then routes each tree over its
+// pairs from the landing zone and adds the bin counts to the job's shared
+// counts with one atomic per (tree, bin) per tile.  Pair p covers samples
+// 64p .. 64p + 63 of the zone.  With uint16 ranks its chunks are the even and
+// the odd samples: lane l reads one word holding samples 64p + 2l and
+// 64p + 2l + 1, the geometry of the re-laid tile (one root load per pair, no
+// bank conflicts, masks [pair][q][lane][chunk]) without a re-layout pass.  With
+// uint32 ranks they are the first and the second 32 samples (masks
+// [chunk][q][lane]).  jb0: byte offset of the zone from the row addresses held
+// in the node table.
 template <int W, int D, int Q>
 __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair, uint32_t jb0,
                                             const uint2* nodes_s, uint32_t nodes_sa,
@@ -43,27 +49,45 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
                                             const uint32_t (&cst)[Q][D], uint32_t* cnt_s, int LK,
                                             int lane, int warp, int ncw) {
   constexpr int B = (1 << D) - 1;
-  typedef PairGeom<W, true> G;
+  constexpr bool EO = (W == 2);  // even/odd chunks on words shared by a pair
+  typedef PairGeom<W, !EO> G;
   if (warp >= npair) return;
+  auto put = [&](int c, int q, uint32_t m) {
+    if (EO)
+      aux32[((c >> 1) * Q + q) * 64 + lane * 2 + (c & 1)] = m;
+    else
+      aux32[(c * Q + q) * 32 + lane] = m;
+  };
   if (K == 2 && lab_done >= 64 * npair) {
     // two classes, every label of the tile landed: all bins of a lane have
-    // class lane % 2 (bin lane + 32 q), so one pair of ballots serves them
+    // class lane % 2 (bin lane + 32 q), so one pair of ballots per chunk
+    // serves them
     const bool odd = lane & 1;
     for (int pp = warp; pp < npair; pp += ncw) {
+      uint32_t ya, yb;
+      if (EO) {
+        const uint32_t l2 = *reinterpret_cast<const uint16_t*>(lab_land + 64 * pp + 2 * lane);
+        ya = l2 & 0xFFu;
+        yb = l2 >> 8;
+      } else {
+        ya = lab_land[64 * pp + lane];
+        yb = lab_land[64 * pp + 32 + lane];
+      }
+      const uint32_t a1 = __ballot_sync(0xFFFFFFFFu, ya == 1u);
+      const uint32_t a0 = __ballot_sync(0xFFFFFFFFu, ya == 0u);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, yb == 1u);
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, yb == 0u);
+      const uint32_t ma = odd ? a1 : a0, mb = odd ? b1 : b0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * pp + h;
-        const uint32_t y = lab_land[c * 32 + lane];
-        const uint32_t y1 = __ballot_sync(0xFFFFFFFFu, y == 1u);
-        const uint32_t y0 = __ballot_sync(0xFFFFFFFFu, y == 0u);
-        const uint32_t m = odd ? y1 : y0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = kq[q] >= 0 ? m : 0u;
+      for (int q = 0; q < Q; ++q) {
+        put(2 * pp, q, kq[q] >= 0 ? ma : 0u);
+        put(2 * pp + 1, q, kq[q] >= 0 ? mb : 0u);
       }
     }
   } else {
     for (int c = 2 * warp; c < 2 * npair; c += (c & 1) ? 2 * ncw - 1 : 1) {
-      const uint32_t y = tile_label(P, lab_land, lab_done, s0, c * 32 + lane, ns);
+      const int j = EO ? 64 * (c >> 1) + 2 * lane + (c & 1) : c * 32 + lane;
+      const uint32_t y = tile_label(P, lab_land, lab_done, s0, j, ns);
       uint32_t mine[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) mine[q] = 0u;
@@ -74,7 +98,7 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
           if (kq[q] == k) mine[q] = m;
       }
 #pragma unroll
-      for (int q = 0; q < Q; ++q) aux32[(c * Q + q) * 32 + lane] = mine[q];
+      for (int q = 0; q < Q; ++q) put(c, q, mine[q]);
     }
   }
   __syncwarp();
@@ -90,12 +114,28 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
     uint32_t cnt[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) cnt[q] = 0u;
-    for (int pp = warp; pp < npair; pp += ncw) {
-      const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
-      const uint32_t ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
-      const uint32_t ymB = ymA + Q * 128u;
-      route_pair<W, D, Q, true, false>(jb, n1.x, n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u,
-                                       tnb + 48u, ntnb, ymA, ymB, cst, cnt);
+    auto walk = [&](auto r32) {
+      constexpr bool R32 = decltype(r32)::value;
+      for (int pp = warp; pp < npair; pp += ncw) {
+        const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
+        uint32_t ymA, ymB;
+        if (EO) {
+          ymA = ymB = aux_sa + ((uint32_t)pp * Q * 64u + (uint32_t)lane * 2u) * 4u;
+        } else {
+          ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
+          ymB = ymA + Q * 128u;
+        }
+        route_pair<W, D, Q, !EO, R32>(jb, n1.x, R32 ? (n1.y << 16) : n1.y, n2.x, n2.y, n3.x, n3.y,
+                                      tnb + 32u, tnb + 48u, ntnb, ymA, ymB, cst, cnt);
+      }
+    };
+    if constexpr (EO) {
+      if (n1.y <= 0xFFFFu)
+        walk(std::true_type{});
+      else
+        walk(std::false_type{});
+    } else {
+      walk(std::false_type{});
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -268,13 +308,14 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
                                lab_done, s0, ns, K, kq, cst, cnt_s, LK, lane, warp, ncw);
       } else {
         // larger groups: the tile's class masks once, shared by every warp
+        // (uint16: even/odd chunks on shared words, as in route_share)
         if (!dead)
-          class_masks<Q, false>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp, ncw,
-                                aux32);
+          class_masks<Q, W == 2, W == 2>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp,
+                                         ncw, aux32);
         bar_sync_n(nct);
         if (!dead)
-          route_group<W, D, Q, true>(jv.ntrees, npair, jb0, nodes_s, nodes_sa, aux_sa, cst, cnt_s,
-                                     LK, lane, warp, ncw);
+          route_group<W, D, Q, W == 4>(jv.ntrees, npair, jb0, nodes_s, nodes_sa, aux_sa, cst, cnt_s,
+                                       LK, lane, warp, ncw);
         bar_sync_n(nct);  // no warp rewrites the masks while another still reads them
       }
       __syncwarp();
