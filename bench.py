@@ -44,11 +44,11 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
 # kernel source it was taken on: a hash of the re-laid evaluator kernel's text in
 # csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "7bfa9057e96f5371", "bytes": 363_230_976 + 3_342_848,
+EVAL_TRAFFIC = {"source_sha256_16": "8a41534ad5961d9f", "bytes": 364_075_776 + 4_039_168,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
-                        "shared_pipe_frac": 0.811, "inst_per_chunk": 35.46, "dram_gbs": 33.7,
-                        "dram_frac_of_peak": 0.0050}}
+                        "shared_pipe_frac": 0.811, "inst_per_chunk": 35.46, "dram_gbs": 33.8,
+                        "dram_frac_of_peak": 0.0051}}
 
 
 def _eval_source_hash():
@@ -445,6 +445,72 @@ def run_p_eval(args):
     return 0
 
 
+def run_stream_scan(args):
+    """Single evaluations of 1 and 2 random depth-4 trees on the main workload's ranks for
+    n = 1e6 .. 1e7 (L2 flushed before each launch), beside a torch reduction over the same
+    number of bytes, and a line through the one-tree times: the fixed cost of a launch and
+    its streaming rate."""
+    import torch
+    from paper_2311_06952_gb300 import build as _build
+    from paper_2311_06952_gb300 import datagen, deoct
+    _build.build()
+    torch.cuda.set_device(0)
+    ctx = deoct.Context(0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    reps = max(3, args.steps)
+    rows = []
+    for n in (1_000_000, 2_500_000, 5_000_000, 10_000_000):
+        data = datagen.make_workload(3, n=n)
+        ds = deoct.encode_dataset(ctx, torch.from_numpy(data["X"]).cuda(), torch.from_numpy(data["y"]).cuda(),
+                                  2, 2)
+        nu = ds.n_unique.cpu().numpy().view(np.uint32)
+        F = data["X"].shape[1]
+        nbytes = n * (2 * F + 1)
+        row = {"n": n, "alg_bytes": nbytes}
+        for P in (1, 2):
+            a, th = datagen.random_population(nu, P, 4, np.random.Generator(np.random.PCG64(50 + P)))
+            ad = torch.from_numpy(a.astype(np.int16)).cuda()
+            td = torch.from_numpy(th.view(np.int32)).cuda()
+            ms = []
+            for it in range(args.warmup + reps):
+                flush.fill_(it & 255)
+                ctx.reset_stats()
+                ctx.set_timing(True)
+                deoct.deoct_eval_population(ctx, ds, ad, td, 4)
+                torch.cuda.synchronize()
+                st = ctx.stats()
+                ctx.set_timing(False)
+                if it >= args.warmup:
+                    ms.append(st["eval_ms"] / max(1, st["eval_timed"]))
+            row["P%d_us" % P] = 1000.0 * float(np.median(ms))
+        x = torch.rand(nbytes // 4, device="cuda")
+        ts = []
+        for it in range(args.warmup + reps):
+            flush.fill_(it & 255)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x.sum()
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        row["torch_sum_us"] = 1000.0 * float(np.median(ts))
+        rows.append(row)
+        del ds, x
+        torch.cuda.empty_cache()
+    peaks, kind = _peaks()
+    nb = np.array([r["alg_bytes"] for r in rows], dtype=np.float64)
+    t1 = np.array([r["P1_us"] for r in rows])
+    slope, fixed = np.polyfit(nb, t1, 1)
+    rate = 1e-3 / slope  # bytes per us -> GB/s
+    print(json.dumps({"mode": "stream-scan", "rows": rows, "P1_fixed_us": float(fixed),
+                      "P1_stream_gbs": float(rate), "P1_stream_frac": float(rate / peaks["hbm_gbs"]),
+                      "peak_kind": kind}), flush=True)
+    ctx.close()
+    return 0
+
+
 PAPER_TABLE3_S = {  # MH-DEOCT training time on an A100 (Table 3), seconds, D = 2 / 4 / 8
     "bitcoin-heist": (77.22, 259.98, 1633.93), "susy": (164.03, 399.88, 5100.47),
     "higgs": (333.01, 1049.87, 15885.24)}
@@ -627,6 +693,8 @@ def main():
     ap.add_argument("--table3", default="", help="comma list of bitcoin-heist,susy,higgs")
     ap.add_argument("--mh-only", action="store_true", help="only the batched-vs-plain moving-horizon line")
     ap.add_argument("--p-eval", type=int, default=0, help="only single evaluations of this many trees")
+    ap.add_argument("--stream-scan", action="store_true",
+                    help="only single evaluations of 1 and 2 trees for n = 1e6..1e7 beside a torch reduction")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -636,6 +704,8 @@ def main():
         return run_table3(args)
     if args.p_eval:
         return run_p_eval(args)
+    if args.stream_scan:
+        return run_stream_scan(args)
     if args.mh_only:
         import torch
         torch.cuda.set_device(0)
