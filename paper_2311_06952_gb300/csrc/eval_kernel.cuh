@@ -183,7 +183,7 @@ __device__ __forceinline__ uint32_t tile_offset(uint32_t j) {
 // kernel; uint16 lanes then pair up on 32-bit words, at most 2-way conflicts).
 // kShared: the re-laid uint16 tile, where the pair's two samples of a row
 // share one 32-bit word (the root is then read once for both chunks, the class
-// masks of the pair sit side by side, and with one bin per lane the pair loop
+// masks of the pair sit side by side, and with few bins per lane the pair loop
 // is unrolled by two).
 template <int W, bool NAT>
 struct PairGeom {
@@ -350,7 +350,9 @@ __device__ __forceinline__ void route_group(int nt, int npair, uint32_t jb0, con
       };
       auto walk = [&](auto r32) {
         int pp = sl;
-        if constexpr (Q == 1) {  // by two (more bins per lane would spill)
+        // by two with one bin per lane, or two at depth <= 3 (measured: 3.8%
+        // faster at depth 3, 1.5% slower at depth 4, where it spills)
+        if constexpr (Q == 1 || (Q == 2 && D <= 3)) {
           for (; pp + step < npair; pp += 2 * step) {
             one(pp, r32);
             one(pp + step, r32);
