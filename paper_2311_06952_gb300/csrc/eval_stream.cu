@@ -52,6 +52,7 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
   constexpr bool EO = (W == 2);  // even/odd chunks on words shared by a pair
   typedef PairGeom<W, !EO> G;
   if (warp >= npair) return;
+  const bool sc = shared_class<D, Q>(LK);
   auto put = [&](int c, int q, uint32_t m) {
     if (EO)
       aux32[((c >> 1) * Q + q) * 64 + lane * 2 + (c & 1)] = m;
@@ -114,7 +115,7 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
     uint32_t cnt[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) cnt[q] = 0u;
-    auto walk = [&](auto r32) {
+    auto walk = [&](auto r32, auto scc) {
       constexpr bool R32 = decltype(r32)::value;
       for (int pp = warp; pp < npair; pp += ncw) {
         const uint32_t jb = jb0 + (uint32_t)pp * G::kPairStride + (uint32_t)lane * G::kLane;
@@ -125,17 +126,27 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
           ymA = aux_sa + ((uint32_t)(2 * pp) * Q * 32u + lane) * 4u;
           ymB = ymA + Q * 128u;
         }
-        route_pair<W, D, Q, !EO, R32>(jb, n1.x, R32 ? (n1.y << 16) : n1.y, n2.x, n2.y, n3.x, n3.y,
-                                      tnb + 32u, tnb + 48u, ntnb, ymA, ymB, cst, cnt);
+        route_pair<W, D, Q, !EO, R32, decltype(scc)::value>(
+            jb, n1.x, R32 ? (n1.y << 16) : n1.y, n2.x, n2.y, n3.x, n3.y, tnb + 32u, tnb + 48u, ntnb,
+            ymA, ymB, cst, cnt);
       }
+    };
+    auto walk_sc = [&](auto r32) {
+      if constexpr (Q == 2 || Q == 4) {
+        if (sc) {
+          walk(r32, std::true_type{});
+          return;
+        }
+      }
+      walk(r32, std::false_type{});
     };
     if constexpr (EO) {
       if (n1.y <= 0xFFFFu)
-        walk(std::true_type{});
+        walk_sc(std::true_type{});
       else
-        walk(std::false_type{});
+        walk_sc(std::false_type{});
     } else {
-      walk(std::false_type{});
+      walk_sc(std::false_type{});
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {

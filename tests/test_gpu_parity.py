@@ -434,6 +434,30 @@ def test_eval_small_groups_streaming_bit_exact(c, depth, K, rb):
                 c.set_eval_config(0, 0, 0, 0)
 
 
+@pytest.mark.parametrize("depth,K", [(4, 4), (4, 8), (3, 8), (3, 16), (5, 2), (5, 4), (2, 32)])
+@pytest.mark.parametrize("rb", [2, 4])
+def test_eval_shared_class_bins_bit_exact(c, depth, K, rb):
+    """Shapes whose bins fill whole lanes with K dividing 32 (2^D K = 32 Q, Q = 2 or 4): every
+    bin of a lane has the same class and the bins differ only in their top leaf levels, so the
+    evaluator ANDs the class mask and the deeper levels once per lane.  Both kernels (P = 1, 3
+    and 6 stream, 24 is re-laid), both rank widths, a ragged tail."""
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(1300 + 10 * depth + K + rb)
+    n, F = 30_011, 6
+    X = np.round(rng.random((n, F)), 4).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    ds = gpu_dataset(c, X, y, K, rb)
+    for P in (1, 3, 6, 24):
+        a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+        ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+        _, ref_err, _, _ = oracle.fitness(ref, a, n)
+        counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th),
+                                                     depth)
+        np.testing.assert_array_equal(u32(counts), ref)
+        np.testing.assert_array_equal(u32(errors), ref_err)
+
+
 def test_bounded_wait_timeout_is_reported_and_context_recovers(c):
     """Failure detection without a fault: a device wait on an mbarrier that nothing arrives on
     runs out after its bound, the next sync check reports DEOCT_ERR_TIMEOUT and clears the
