@@ -44,7 +44,7 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
 # kernel source it was taken on: a hash of the re-laid evaluator kernel's text in
 # csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "7092bd99a6d0a070", "bytes": 364_257_280 + 3_513_088,
+EVAL_TRAFFIC = {"source_sha256_16": "0ace87716ed27363", "bytes": 362_880_256 + 3_740_160,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
                         "shared_pipe_frac": 0.810, "inst_per_chunk": 35.46, "dram_gbs": 33.8,
