@@ -42,26 +42,53 @@ WORKLOAD = dict(workload="large-deoct: n=1e7, F=10 U(0,1) quantised to 60000 lev
 INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # DRAM bytes (read + write) of one evaluator launch on this workload, from the ncu
 # capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
-# kernel source it was taken on: a hash of the re-laid evaluator kernel's text in
-# csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh).
-EVAL_TRAFFIC = {"source_sha256_16": "0ace87716ed27363", "bytes": 362_880_256 + 3_740_160,
+# kernel code it was taken on: a hash of the re-laid evaluator kernel's code in
+# csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh),
+# comments and whitespace left out.
+EVAL_TRAFFIC = {"source_sha256_16": "a4c4dbcf0c09479c", "bytes": 362_880_256 + 3_740_160,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
                         "shared_pipe_frac": 0.810, "inst_per_chunk": 35.46, "dram_gbs": 33.8,
                         "dram_frac_of_peak": 0.0051}}
 
 
+def _strip_comments(src):
+    """C/C++ source without comments and with runs of whitespace collapsed: the code an
+    ncu capture depends on, not its documentation."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _eval_source_hash():
+    """Key of the evaluator kernel's code: the `eval_kernel` template of csrc/eval.cu and
+    the headers it is built from, comments and whitespace left out."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2311_06952_gb300", "csrc")
     ev = open(os.path.join(csrc, "eval.cu")).read()
     a = ev.index("__global__ void __launch_bounds__(512, 2) eval_kernel(")
     a = ev.rindex("template", 0, a)
     b = ev.index("int launch_t(", a)
-    h = hashlib.sha256(ev[a:b].encode())
+    h = hashlib.sha256(_strip_comments(ev[a:b]).encode())
     for f in ("eval_kernel.cuh", "common.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -179,12 +179,14 @@ __device__ __forceinline__ uint32_t tile_offset(uint32_t j) {
   return (j >> 6) * 128u + (j & 31u) * 4u + ((j >> 5) & 1u) * 2u;
 }
 // Where lane l finds the two samples of chunk pair p: at p * kPairStride +
-// l * kLane and kSecond bytes further.  NAT: natural sample order (streaming
-// kernel; uint16 lanes then pair up on 32-bit words, at most 2-way conflicts).
-// kShared: the re-laid uint16 tile, where the pair's two samples of a row
-// share one 32-bit word (the root is then read once for both chunks, the class
-// masks of the pair sit side by side, and with few bins per lane the pair loop
-// is unrolled by two).
+// l * kLane and kSecond bytes further.  NAT: the two chunks are the first and
+// the second 32 samples of the pair in natural order (the streaming kernel's
+// uint32 tiles; for uint16 this geometry would put two lanes on one bank word).
+// kShared: uint16 rows whose words each hold a sample of both chunks -- the
+// re-laid tile (samples 64p + l and 64p + 32 + l) or the streaming kernel's
+// landing zone read as even/odd chunks (64p + 2l and 64p + 2l + 1); the root is
+// then read once for both chunks, the class masks of the pair sit side by
+// side, and with few bins per lane the pair loop is unrolled by two.
 template <int W, bool NAT>
 struct PairGeom {
   static constexpr uint32_t kSecond = (W == 4) ? 128u : (NAT ? 64u : 2u);
