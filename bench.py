@@ -659,9 +659,12 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     eval_ms = st["eval_ms"] / max(1, st["eval_timed"])
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    ops_per_eval = 2 * D + 1  # Algorithm 1: per level one comparison + one child step; one count
+    # per tree-sample evaluation, per level: load the node's feature and threshold, load the
+    # sample's rank, compare, step to the child; then the count increment (2)
+    ops_per_eval = 4 * D + 2
     ops_per_launch = ops_per_eval * P * n
     achieved = ops_per_launch / (eval_ms / 1000.0) / 1e12
+    strict_ops = (2 * D + 1) * P * n  # only the comparison and the child step per level, one count
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     peak = nsm * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     bytes_per_launch = n * (F * 2 + 1)
@@ -676,7 +679,11 @@ def run_ours(args):
                      "traffic": args.traffic if args.traffic is not None else (
                          _traffic_default() if args.n == WORKLOAD["n"] else None),
                      "kernel": "eval_kernel<2,4,0> (population evaluator)",
-                     "ops_per_launch": ops_per_launch, "launch_ms": eval_ms,
+                     "ops_per_launch": ops_per_launch, "ops_per_eval": ops_per_eval,
+                     "launch_ms": eval_ms,
+                     "strict_view": {"ops_per_eval": 2 * D + 1, "ops_per_launch": strict_ops,
+                                     "achieved": strict_ops / (eval_ms / 1000.0) / 1e12,
+                                     "frac": strict_ops / (eval_ms / 1000.0) / 1e12 / peak},
                      "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz (%s max clock)" % (
                          nsm, INT32_LANES_PER_SM, sm_mhz, peak_kind),
                      "issue_view": _ncu_default() if args.n == WORKLOAD["n"] else None,
