@@ -124,30 +124,73 @@ __global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
   if (threadIdx.x == 0 && pb.gen) *pb.gen = 1;
 }
 
-__global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags) {
+// The fitness of individual r by its group of G lanes (G a power of two that
+// divides 32; `sub` the lane's place in the group, `gm` the group's lane mask):
+// each lane takes leaves sub, sub + G, ... and genes sub, sub + G, ..., and the
+// integer partial sums meet by shuffles, so every lane returns the value
+// fitness_of gives.
+__device__ double group_fitness(const uint32_t* __restrict__ c, const float* __restrict__ genes,
+                                int B, int L, int K, int64_t n_valid, int n_min, double alpha,
+                                int sub, int G, uint32_t gm) {
+  long long correct = 0;
+  uint32_t v = 0, splits = 0;
+  for (int l = sub; l < L; l += G) {
+    uint32_t mx = 0;
+    int64_t nl = 0;
+    for (int k = 0; k < K; ++k) {
+      const uint32_t x = c[l * K + k];
+      mx = x > mx ? x : mx;
+      nl += x;
+    }
+    correct += mx;
+    if (nl > 0 && nl < n_min) v += 1;
+  }
+  for (int t = sub; t < B; t += G) splits += genes[t] >= 1.0f ? 1u : 0u;
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    correct += __shfl_xor_sync(gm, correct, o);
+    v += __shfl_xor_sync(gm, v, o);
+    splits += __shfl_xor_sync(gm, splits, o);
+  }
+  const int64_t errors = n_valid - (int64_t)correct;
+  return __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(alpha, (double)splits));
+}
+
+// One CTA per subproblem; each individual is worked on by a group of `lanes`
+// consecutive threads (lanes x P <= blockDim.x), which shortens the chain of
+// dependent loads one thread would walk alone.  Every value is the one a
+// single thread computes: integer sums, the draws of a (generation,
+// individual, block) Philox key, one rounding per float operation.
+__global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags,
+                                                       int lanes) {
   __shared__ double red_f[32];
   __shared__ int red_i[32];
   __shared__ int best_s;
   __shared__ int g_s;
   const DEProb& pb = prob_of(a);
   const int P = a.P, D = a.depth, B = (1 << D) - 1, m = 2 * B, L = 1 << D, K = pb.K;
+  const int G = lanes;
+  const int sub = threadIdx.x & (G - 1);
+  const uint32_t gm = (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+  const int r0 = threadIdx.x / G, rstep = blockDim.x / G;
 
   if (threadIdx.x == 0) g_s = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
 
   if (flags & (DE_FIRST | DE_SELECT)) {
     const bool first = (flags & DE_FIRST) != 0;
-    for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    for (int r = r0; r < P; r += rstep) {
       const float* genes = (first ? pb.pop : pb.trial) + (int64_t)r * m;
-      const double f = fitness_of(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
-                                  a.n_min, a.alpha);
+      const double f = group_fitness(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
+                                     a.n_min, a.alpha, sub, G, gm);
       if (first) {
-        pb.fit[r] = f;
+        if (sub == 0) pb.fit[r] = f;
       } else {
-        pb.fit_trial[r] = f;
-        if (f <= pb.fit[r]) {  // Eq. selection: ties go to the trial
+        const double fr = pb.fit[r];
+        __syncwarp(gm);
+        if (sub == 0) pb.fit_trial[r] = f;
+        if (f <= fr) {  // Eq. selection: ties go to the trial
           float* dst = pb.pop + (int64_t)r * m;
-          for (int q = 0; q < m; ++q) dst[q] = genes[q];
-          pb.fit[r] = f;
+          for (int q = sub; q < m; q += G) dst[q] = genes[q];
+          if (sub == 0) pb.fit[r] = f;
         }
       }
     }
@@ -166,11 +209,12 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   const float ub_a = (float)(pb.F + 1);
   const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
   const float* sb = pb.pop + (int64_t)best * m;
-  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+  const int per = (m + G - 1) / G;  // consecutive genes per lane: they share Philox blocks
+  for (int r = r0; r < P; r += rstep) {
     // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
-    U64x4 blk = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
-    const uint32_t x0 = draw_from_block(blk, 0), x1 = draw_from_block(blk, 1);
-    const uint32_t x2 = draw_from_block(blk, 2), x3 = draw_from_block(blk, 3);
+    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
+    const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
+    const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
     int r1 = (int)below(x0, (uint32_t)(P - 1));
     if (r1 >= r) r1 += 1;
     int r2 = (int)below(x1, (uint32_t)(P - 2));
@@ -183,17 +227,22 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
     const float* s2 = pb.pop + (int64_t)r2 * m;
     const float* sr = pb.pop + (int64_t)r * m;
     float* u = pb.trial + (int64_t)r * m;
-    for (int q = 0; q < m; ++q) {
+    U64x4 blk = blk0;
+    uint32_t cur = 0;  // block held in blk
+    const int q0 = sub * per, q1 = min(m, q0 + per);
+    for (int q = q0; q < q1; ++q) {
       const uint32_t s = 4u + (uint32_t)q;
-      if ((s & 7u) == 0u)
-        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)(s >> 3), 0ull, a.seed,
-                            pb.stream_id);
+      if ((s >> 3) != cur) {
+        cur = s >> 3;
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, a.seed, pb.stream_id);
+      }
       const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
       const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
       const float rq = u01(draw_from_block(blk, s));
       u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
     }
-    for (int t = 0; t < B; ++t) {
+    __syncwarp(gm);  // the group's genes are written before they are decoded
+    for (int t = sub; t < B; t += G) {
       int av;
       uint32_t th;
       decode_gene_pair(u[t], u[B + t], pb.F, pb.n_unique, &av, &th);
@@ -235,6 +284,14 @@ __global__ void best_extract_kernel(const float* __restrict__ pop, const double*
   if (threadIdx.x == 0) *fit_out = fit[b];
 }
 
+// Threads per individual in the step kernel: the largest power of two up to 8
+// that keeps the CTA within 1024 threads (8 for P <= 128, 1 for P > 512).
+int lanes_for(int P) {
+  int g = 1;
+  while (g < 8 && P * g * 2 <= 1024) g *= 2;
+  return g;
+}
+
 int block_for(int P) {
   int b = ((P + 31) / 32) * 32;
   if (b > 1024) b = 1024;
@@ -255,7 +312,8 @@ int de_launch_init(deoct_ctx* ctx, const DEArgs& a, cudaStream_t s) {
 int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream_t s) {
   const int nprob = a.probs ? a.nprob : 1;
   if (nprob <= 0) return DEOCT_OK;
-  de_step_kernel<<<nprob, block_for(a.P), 0, s>>>(a, g, flags);
+  const int lanes = lanes_for(a.P);
+  de_step_kernel<<<nprob, block_for(a.P * lanes), 0, s>>>(a, g, flags, lanes);
   count_launch(ctx);
   return check_launch("de_step_kernel");
 }

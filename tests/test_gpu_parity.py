@@ -238,6 +238,8 @@ DE_CASES = [
     ("w0", 3, 32, 25, 0.1, True, False, 7, 5),
     ("w0", 2, 16, 30, 0.5, False, True, 3, 9),
     ("rand_k3", 3, 24, 20, 0.9, False, False, 11, 1),
+    ("w0", 2, 200, 8, 0.9, False, False, 2, 4),        # 4 threads per individual in the step
+    ("rand_k3", 3, 300, 5, 0.5, True, False, 13, 6),   # 2 threads per individual
 ]
 
 
