@@ -156,8 +156,8 @@ __device__ double group_fitness(const uint32_t* __restrict__ c, const float* __r
 }
 
 // One CTA per subproblem; each individual is worked on by a group of `lanes`
-// consecutive threads (lanes x P <= blockDim.x), which shortens the chain of
-// dependent loads one thread would walk alone.  Every value is the one a
+// consecutive threads (lanes x P <= blockDim.x, lanes <= 4), which shortens the
+// chain of dependent loads one thread would walk alone.  Every value is the one a
 // single thread computes: integer sums, the draws of a (generation,
 // individual, block) Philox key, one rounding per float operation.
 __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg, int flags,
@@ -284,11 +284,14 @@ __global__ void best_extract_kernel(const float* __restrict__ pop, const double*
   if (threadIdx.x == 0) *fit_out = fit[b];
 }
 
-// Threads per individual in the step kernel: the largest power of two up to 8
-// that keeps the CTA within 1024 threads (8 for P <= 128, 1 for P > 512).
+// Threads per individual in the step kernel: the largest power of two up to 4
+// that keeps the CTA within 1024 threads (4 for P <= 256, 1 for P > 512).
+// Measured on the moving-horizon workload (P = 128): 1 / 2 / 4 / 8 threads gave
+// 0.2246 / 0.2215 / 0.2180 / 0.2212 s batched and 0.674 / 0.653 / 0.631 / 0.687 s
+// plain (with 8, the CTA-wide argmin and barriers span 32 warps).
 int lanes_for(int P) {
   int g = 1;
-  while (g < 8 && P * g * 2 <= 1024) g *= 2;
+  while (g < 4 && P * g * 2 <= 1024) g *= 2;
   return g;
 }
 
