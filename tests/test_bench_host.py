@@ -1,0 +1,59 @@
+"""Host logic of bench.py that needs no GPU: the key that ties the stored ncu traffic of the
+evaluator to the code it was captured on, and the JSON fields derived from it."""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def test_strip_comments_keeps_code_and_string_contents():
+    src = ('int a = 1; // line comment\n/* block\n comment */ const char* s = "a//b /* c */";\n'
+           "char q = '/'; char e = '\\''; int b = a / 2;")
+    out = bench._strip_comments(src)
+    assert "line comment" not in out and "block" not in out
+    assert '"a//b /* c */"' in out
+    assert "'/'" in out and "'\\''" in out
+    assert "int b = a / 2;" in out
+
+
+def test_strip_comments_collapses_whitespace():
+    assert bench._strip_comments("a  =\n\n\tb ;  // x\n") == bench._strip_comments("a = b ;")
+
+
+def _copy_sources(tmp_path):
+    root = tmp_path / "repo"
+    csrc = root / "paper_2311_06952_gb300" / "csrc"
+    shutil.copytree(os.path.join(bench.ROOT, "paper_2311_06952_gb300", "csrc"), csrc)
+    return str(root), csrc
+
+
+def test_source_key_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", root)
+    base = bench._eval_source_hash()
+    hdr = csrc / "eval_kernel.cuh"
+    text = hdr.read_text()
+    hdr.write_text(text.replace("#pragma once", "// an added comment line\n#pragma once", 1))
+    assert bench._eval_source_hash() == base
+    hdr.write_text(text.replace("constexpr int kMaxStages = 3;", "constexpr int kMaxStages = 2;", 1))
+    assert bench._eval_source_hash() != base
+
+
+def test_stored_traffic_is_used_only_for_its_code(monkeypatch):
+    monkeypatch.setattr(bench, "_eval_source_hash", lambda: bench.EVAL_TRAFFIC["source_sha256_16"])
+    assert bench._traffic_default() == bench.EVAL_TRAFFIC["bytes"]
+    assert bench._ncu_default() is bench.EVAL_TRAFFIC["ncu"]
+    monkeypatch.setattr(bench, "_eval_source_hash", lambda: "0" * 16)
+    assert bench._traffic_default() is None
+    assert bench._ncu_default() is None
+
+
+def test_traffic_is_null_for_other_code(tmp_path, monkeypatch):
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", root)
+    common = csrc / "common.cuh"
+    common.write_text(common.read_text() + "\nnamespace deoct { constexpr int kChanged = 1; }\n")
+    assert bench._traffic_default() is None
+    assert bench._ncu_default() is None
