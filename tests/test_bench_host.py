@@ -3,7 +3,6 @@ evaluator to the code it was captured on, and the JSON fields derived from it.""
 import os
 import shutil
 
-import pytest
 
 import bench
 
