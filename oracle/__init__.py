@@ -15,12 +15,15 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
   encode, decode, eval_counts, fitness, leaf_classes, depth1 -- pinned (numpy.unique,
       float-midpoint routing of Eq. benc, brute force, the loss identity of Section 2);
   philox / draw32 -- pinned to numpy's Philox4x64-10 bit generator;
-  de_run -- pinned by invariants only (selection monotonicity, gene ranges,
-      mutation/crossover membership, Philox stream); the draw-to-index map and
-      the clamp of out-of-range mutants are readings, "parity unpinned" beyond those;
+  de_trial, de_run -- Eq. mutation, Eq. crossover, the clamp and the initial
+      population pinned bit for bit to a numpy float32 restatement driven by
+      numpy's own Philox stream, plus closed forms (CR = 1, CR = 0, M = 0) and the
+      invariants of selection; the draw-to-index maps and the clamp are readings
+      of the paper (its text fixes neither), pinned as stated;
+  node_genes -- decodes back to every (a, theta) under Eq. aenc / Eq. benc;
   mh -- pinned by special cases (horizon 1 = greedy misclassification tree,
-      n_min >= n, single class); the DE-solved nodes are "parity unpinned"
-      beyond the DE invariants.
+      n_min >= n, single class) and by Algorithm 2 restated in Python over the
+      pinned de_run and depth1 (subsets induced on raw float thresholds).
 """
 from __future__ import annotations
 
@@ -251,6 +254,19 @@ def greedy_tree(ranks, n_unique, y, K, depth, idx=None, n_min=1, alpha=0.0):
     if rc != ORC_OK:
         raise ValueError("oracle greedy_tree failed: %d" % rc)
     return a, th
+
+
+def node_genes(a, theta, n_p):
+    """Genes of decoded nodes (the inverse of Eq. aenc / Eq. benc used for warm starts):
+    a, theta, n_p [m] -> (ahat [m] float32, bhat [m] float32)."""
+    a = _c(a, np.int32)
+    theta = _c(theta, np.uint32)
+    n_p = _c(n_p, np.uint32)
+    m = len(a)
+    ah = np.empty(m, np.float32)
+    bh = np.empty(m, np.float32)
+    lib().orc_node_genes(_p(a), _p(theta), _p(n_p), ctypes.c_int64(m), _p(ah), _p(bh))
+    return ah, bh
 
 
 def mh(ranks, n_unique, y, K, depth, horizon, P, G, M=0.5, CR=0.9, alpha=0.0, n_min=1, seed=0,

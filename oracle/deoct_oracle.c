@@ -20,9 +20,9 @@
  * Parity pins: every function below is checked by tests/test_oracle_*.py
  * against something other than itself (numpy.unique, numpy's Philox bit
  * generator, brute force over all trees, float-midpoint routing, invariants of
- * the loss).  The DE trajectory and the moving-horizon driver are pinned only
- * partly (invariants, special cases, Philox stream); their remaining
- * conventions are readings, not paper facts.
+ * the loss, a numpy float32 restatement of the DE trial and initialisation).
+ * The moving-horizon driver is pinned by special cases; the conventions it and
+ * the DE step fix where the paper is silent are readings, not paper facts.
  */
 #include <math.h>
 #include <stdint.h>
@@ -524,6 +524,15 @@ int orc_greedy_tree(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t*
 /* Genes of a decoded node (inverse of Eq. aenc / Eq. benc): ahat = a + 1/2;
  * bhat = the float32 nearest (theta + 1/2) / (n_p + 1), moved one float at a
  * time until floor(bhat (n_p + 1)) = theta. */
+static void node_genes(int32_t a, uint32_t theta, uint32_t np, float* ahat, float* bhat);
+
+/* node_genes over m nodes: a [m], theta [m], np [m] (n_p of each node's
+ * feature, 1 for a = 0) -> ahat [m], bhat [m]. */
+void orc_node_genes(const int32_t* a, const uint32_t* theta, const uint32_t* np, int64_t m,
+                    float* ahat, float* bhat) {
+  for (int64_t i = 0; i < m; ++i) node_genes(a[i], theta[i], np[i], &ahat[i], &bhat[i]);
+}
+
 static void node_genes(int32_t a, uint32_t theta, uint32_t np, float* ahat, float* bhat) {
   *ahat = (float)a + 0.5f;
   if (a == 0) { *bhat = 0.0f; return; }

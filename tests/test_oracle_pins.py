@@ -404,6 +404,164 @@ def test_de_seeds_occupy_first_slots():
 
 
 # --------------------------------------------------------------------------
+# DE arithmetic (Algorithm 4, Eq. mutation, Eq. crossover, initialisation)
+# restated in numpy float32 with draws from numpy's own Philox4x64-10
+# --------------------------------------------------------------------------
+
+_TWO_M24 = np.float32(2.0 ** -24)
+
+
+def _np_draws(seed, stream, g, r, nslots):
+    """The 32-bit draws of (g, r): block b is numpy's Philox4x64-10 at counter (g, r, b, 0)
+    and key (seed, stream), split into eight halves, low half first (Reading C5)."""
+    out = []
+    for b in range((nslots + 7) // 8):
+        for w in _numpy_philox_block((g, r, b, 0), (seed, stream)):
+            out += [int(w) & 0xFFFFFFFF, int(w) >> 32]
+    return out[:nslots]
+
+
+def _np_u01(x):
+    return np.float32(x >> 8) * _TWO_M24  # 24 bits times 2^-24: exact in float32
+
+
+def _np_hi(q, B, F):
+    return np.nextafter(np.float32(F + 1 if q < B else 1.0), np.float32(0))
+
+
+def _np_trial(pop, best, g, r, F, B, M, CR, seed, stream, dither):
+    """Eq. mutation v = s_best + M (s_r1 - s_r2), each operation rounded to float32; the clamp
+    of Reading C6; Eq. crossover u_q = v_q if rand_q <= CR or q = q_rand, else s_{r,q}."""
+    P, m = pop.shape
+    x = _np_draws(seed, stream, g, r, 4 + m)
+    r1 = (x[0] * (P - 1)) >> 32
+    r1 += r1 >= r
+    r2 = (x[1] * (P - 2)) >> 32
+    for skip in sorted((r, r1)):
+        r2 += r2 >= skip
+    qrand = (x[2] * m) >> 32
+    Mf = _np_u01(x[3]) if dither else np.float32(M)
+    v = pop[best] + Mf * (pop[r1] - pop[r2])  # float32 arrays: one rounding per operation
+    assert v.dtype == np.float32
+    hi = np.array([_np_hi(q, B, F) for q in range(m)], np.float32)
+    v = np.minimum(np.maximum(v, np.float32(0)), hi)
+    rand = np.array([_np_u01(x[4 + q]) for q in range(m)], np.float32)
+    take = (rand <= np.float32(CR)) | (np.arange(m) == qrand)
+    return np.where(take, v, pop[r]), r1, r2, qrand
+
+
+def _extreme_population(rng, P, B, F):
+    """Genes at 0 or just below the bound half of the time, so that mutants leave the gene
+    range on both sides and the clamp of Reading C6 is exercised."""
+    pop = datagen.random_genes(P, int(np.log2(B + 1)), F, rng)
+    hi = np.array([_np_hi(q, B, F) for q in range(2 * B)], np.float32)
+    pick = rng.random(pop.shape)
+    pop = np.where(pick < 0.25, np.float32(0), np.where(pick > 0.75, hi[None, :], pop))
+    return pop.astype(np.float32)
+
+
+@pytest.mark.parametrize("dither,CR,M", [(False, 0.9, 0.5), (False, 0.3, 0.7), (True, 0.6, 0.0),
+                                         (False, 1.0, 1.3)])
+def test_de_trial_equals_numpy_restatement(dither, CR, M):
+    """Eq. mutation and Eq. crossover bit for bit against a numpy float32 restatement whose
+    draws come from numpy's Philox (not from the oracle's draw32)."""
+    rng = _rng(21)
+    F, depth = 6, 3
+    B = 7
+    clamped_lo = clamped_hi = 0
+    for P in (4, 5, 17, 64):
+        pop = _extreme_population(rng, P, B, F)
+        for g in (1, 2, 9, 1000):
+            best = int(rng.integers(P))
+            for r in range(P):
+                u, r1, r2, qr = oracle.de_trial(pop, best, g, r, F, depth, M=M, CR=CR, seed=7,
+                                                stream=3, dither=dither)
+                want, w1, w2, wq = _np_trial(pop, best, g, r, F, B, M, CR, 7, 3, dither)
+                assert (r1, r2, qr) == (w1, w2, wq)
+                np.testing.assert_array_equal(u.view(np.uint32), want.view(np.uint32))
+                raw = pop[best] + np.float32(M) * (pop[r1] - pop[r2])
+                clamped_lo += int(np.sum(raw < 0))
+                clamped_hi += int(np.sum(raw > np.array([_np_hi(q, B, F) for q in range(2 * B)])))
+    if M != 0.0 and not dither:
+        assert clamped_lo > 0 and clamped_hi > 0
+
+
+def test_de_trial_closed_forms():
+    """Facts of Eq. mutation / Eq. crossover that hold whatever the draws are: with CR = 1
+    every gene is the (clamped) mutant s_best + M (s_r1 - s_r2); with CR = 0 only gene q_rand
+    is (a 2^-24 draw aside); with M = 0 every gene is s_best's or s_r's."""
+    rng = _rng(5)
+    F, depth, P = 4, 2, 12
+    B = 3
+    pop = datagen.random_genes(P, depth, F, rng)
+    hi = np.array([_np_hi(q, B, F) for q in range(2 * B)], np.float32)
+    for g in range(1, 30):
+        for r in range(P):
+            best = (g + 3) % P
+            u, r1, r2, qr = oracle.de_trial(pop, best, g, r, F, depth, M=0.8, CR=1.0, seed=1)
+            v = pop[best] + np.float32(0.8) * (pop[r1] - pop[r2])
+            np.testing.assert_array_equal(u, np.clip(v, 0, hi))
+            u0, r1, r2, qr = oracle.de_trial(pop, best, g, r, F, depth, M=0.8, CR=0.0, seed=1)
+            v = np.clip(pop[best] + np.float32(0.8) * (pop[r1] - pop[r2]), 0, hi)
+            for q in range(2 * B):
+                assert u0[q] == (v[q] if q == qr else pop[r, q])
+            uz, _, _, _ = oracle.de_trial(pop, best, g, r, F, depth, M=0.0, CR=0.5, seed=1)
+            assert np.all((uz == pop[best]) | (uz == pop[r]))
+
+
+@pytest.mark.parametrize("S", [0, 2])
+def test_de_initial_population_equals_numpy_restatement(S):
+    """Initial individual r >= S (Algorithm 4): gene q = clamp(u * ub) with u the 24-bit
+    uniform of draw q at generation tag 0 (numpy's Philox), ub = F + 1 for ahat, 1 for bhat."""
+    w = datagen.make_workload(0, n=200)
+    ranks, nu = oracle.encode(w["X"])
+    F, depth, P = 8, 3, 24
+    B = 7
+    seeds = datagen.random_genes(S, depth, F, _rng(2)) if S else None
+    out = oracle.de_run(ranks, nu, w["y"], w["K"], depth=depth, P=P, G=0, seed=11, stream=5,
+                        seeds=seeds, history=True)
+    init = out["pop_hist"][0]
+    for r in range(P):
+        if r < S:
+            np.testing.assert_array_equal(init[r], seeds[r])
+            continue
+        x = _np_draws(11, 5, 0, r, 2 * B)
+        for q in range(2 * B):
+            ub = np.float32(F + 1 if q < B else 1.0)
+            want = min(max(_np_u01(x[q]) * ub, np.float32(0)), _np_hi(q, B, F))
+            assert init[r, q].view(np.uint32) == np.float32(want).view(np.uint32), (r, q)
+    # and the genes are spread over their whole range
+    a_genes = init[S:, :B].ravel() / (F + 1)
+    assert 0.3 < a_genes.mean() < 0.7 and a_genes.max() > 0.8 and a_genes.min() < 0.2
+
+
+@pytest.mark.parametrize("n_p", [1, 2, 3, 7, 1000, 65535, 65536, (1 << 24) - 3])
+def test_node_genes_invert_eq_aenc_benc(n_p):
+    """The warm-start encoding of a node (a, theta) gives genes that decode back to (a, theta)
+    under Eq. aenc (a = floor(ahat)) and Eq. benc (theta = floor(bhat (n_p + 1)), restated here
+    in float64), for every theta of the feature (a sample of them for 2^24 values)."""
+    if n_p <= 65536:
+        th = np.arange(n_p, dtype=np.uint32)
+    else:
+        th = np.unique(np.concatenate([np.arange(300), n_p - 1 - np.arange(300),
+                                       _rng(4).integers(0, n_p, 5000)])).astype(np.uint32)
+    for a in (1, 5):
+        av = np.full(len(th), a, np.int32)
+        ah, bh = oracle.node_genes(av, th, np.full(len(th), n_p, np.uint32))
+        np.testing.assert_array_equal(np.floor(ah).astype(np.int32), av)
+        dec = np.floor(bh.astype(np.float64) * (n_p + 1.0))
+        np.testing.assert_array_equal(np.minimum(dec, n_p - 1), th)
+        assert np.all(bh >= 0) and np.all(bh < 1)
+        # the oracle's decoder agrees (depth 1 trees: [ahat, bhat])
+        nu = np.full(max(a, 5), n_p, np.uint32)
+        da, dt = oracle.decode(np.stack([ah, bh], axis=1), 1, nu)
+        np.testing.assert_array_equal(da[:, 0], av)
+        np.testing.assert_array_equal(dt[:, 0], th)
+    ah, bh = oracle.node_genes(np.zeros(3, np.int32), np.zeros(3, np.uint32), np.ones(3, np.uint32))
+    assert np.all(np.floor(ah) == 0) and np.all(bh == 0)  # no split stays no split
+
+
+# --------------------------------------------------------------------------
 # Algorithm 2 (moving horizon): special cases with a closed form
 # --------------------------------------------------------------------------
 
@@ -488,6 +646,67 @@ def test_mh_root_is_deoct_root_when_horizon_covers_depth():
 # --------------------------------------------------------------------------
 # Raw-unit thresholds and prediction (Section 3.1 threshold set, Section 2 routing)
 # --------------------------------------------------------------------------
+
+def _np_route_to_depth(X, uniq, a, b_idx, d):
+    """BFS node (1-based) that each sample reaches after d levels of the partial tree, routing
+    raw values with x < beta (beta from the threshold set B_p of Section 3.1)."""
+    n = X.shape[0]
+    node = np.ones(n, np.int64)
+    for _ in range(d):
+        left = np.zeros(n, bool)
+        for t in np.unique(node):
+            m = node == t
+            if a[t - 1] > 0:
+                p = a[t - 1] - 1
+                th = b_idx[t - 1]
+                beta = -np.inf if th == 0 else (uniq[p][th - 1] + uniq[p][th]) / 2
+                left[m] = X[m, p].astype(np.float64) < beta
+        node = np.where(left, 2 * node, 2 * node + 1)
+    return node
+
+
+@pytest.mark.parametrize("depth,horizon,seed,n_min", [(4, 2, 0, 1), (4, 3, 1, 1), (5, 3, 2, 12)])
+def test_mh_equals_algorithm2_composed_from_pinned_steps(depth, horizon, seed, n_min):
+    """Algorithm 2 restated in Python on top of the separately pinned DEOCT (de_run) and
+    depth-1 search: nodes in BFS order; (X_t, Y_t) induced by routing raw values through the
+    nodes fixed so far; solve iff |X_t| > n_min and two classes; D_t = min(D_MH, D - d); DEOCT
+    with Philox stream t keeps its best tree's root, depth 1 is the exhaustive search; leaf
+    classes by Eq. opt_c on the whole set."""
+    w = datagen.make_workload(0, n=700)
+    X, y, K = w["X"][:, :5], w["y"], w["K"]
+    rng = _rng(seed)
+    y = np.where(rng.random(len(y)) < 0.1, 1 - y, y).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    uniq = [np.unique(np.where(X[:, p] == 0, 0, X[:, p]).astype(np.float64)) for p in range(X.shape[1])]
+    P, G = 8, 6
+    got = oracle.mh(ranks, nu, y, K, depth, horizon, P, G, seed=seed, n_min=n_min)
+    B = (1 << depth) - 1
+    a = np.zeros(B, np.int64)
+    th = np.zeros(B, np.int64)
+    kind = np.zeros(B, np.int64)
+    for t in range(1, B + 1):
+        d = t.bit_length() - 1
+        idx = np.nonzero(_np_route_to_depth(X, uniq, a, th, d) == t)[0].astype(np.int32)
+        if not (len(idx) > n_min and len(np.unique(y[idx])) > 1):
+            continue
+        Dt = min(horizon, depth - d)
+        if Dt >= 2:
+            out = oracle.de_run(ranks, nu, y, K, depth=Dt, P=P, G=G, seed=seed, stream=t, idx=idx,
+                                n_min=n_min)
+            ga, gt = oracle.decode(out["pop"][out["best"]][None], Dt, nu)
+            a[t - 1], th[t - 1], kind[t - 1] = ga[0, 0], gt[0, 0], 2
+        else:
+            a1, t1, _ = oracle.depth1(ranks, nu, y, K, idx=idx, n_min=n_min)
+            a[t - 1], th[t - 1], kind[t - 1] = a1, t1, 1
+    np.testing.assert_array_equal(got["kind"], kind)
+    np.testing.assert_array_equal(got["a"], a)
+    np.testing.assert_array_equal(got["theta"], th)
+    assert (kind == 2).sum() >= 3 and (kind == 1).sum() >= 1
+    leaf = _np_route_to_depth(X, uniq, a, th, depth) - (B + 1)
+    cnt = np.zeros((1 << depth, K), np.int64)
+    np.add.at(cnt, (leaf, y), 1)
+    np.testing.assert_array_equal(got["leaf_class"], np.argmax(cnt, axis=1))
+
 
 def test_split_values_route_training_samples_like_ranks():
     rng = _rng(61)
