@@ -40,11 +40,11 @@ WORKLOAD = dict(workload="large-deoct: n=1e7, F=10 U(0,1) quantised to 60000 lev
                 n=10_000_000, F=10, K=2, depth=4, pop=1024, gens=50,
                 l2="inputs larger than L2 (X 400 MB, ranks 200 MB); no flush")
 INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
-# DRAM bytes (read + write) of one evaluator launch on this workload, from the ncu
-# capture summarised in profiles/eval_kernel_large_deoct.md; valid only for the
-# kernel code it was taken on: a hash of the re-laid evaluator kernel's code in
-# csrc/eval.cu and of the headers it is built from (eval_kernel.cuh, common.cuh),
-# comments and whitespace left out.
+# DRAM bytes (read + write) of one evaluator launch on this workload, from an ncu
+# capture of the evaluator on this workload; valid only for the kernel code it was
+# taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
+# headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
+# left out.
 EVAL_TRAFFIC = {"source_sha256_16": "a4c4dbcf0c09479c", "bytes": 362_880_256 + 3_740_160,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
@@ -171,47 +171,65 @@ def _dist_setup():
     return rank, world, local
 
 
-def _cpu_baseline(w, budget_s=12.0):
-    """The oracle as it stands on the host's cores: initial evaluation plus one DE
+def _oracle_step(X, y, K, P, D, seed):
+    """One bounded oracle step on host cores: rank encode + initial evaluation + one DE
+    generation of the P-tree population (2 P n tree*sample evaluations)."""
+    import oracle
+    ranks, nu = oracle.encode_omp(X)
+    oracle.de_run(ranks, nu, y, K, depth=D, P=P, G=1, seed=seed)
+
+
+def _cpu_baseline(w, budget_s=15.0):
+    """The oracle on the host's cores (its OpenMP twins: encode per feature, counts per
+    (tree, sample chunk); bit-exact with the plain oracle): initial evaluation plus one DE
     generation of the full population on a bounded prefix of the samples."""
     import oracle
-    P, D = w["pop"], w["depth"]
-    n_try = 4000
-    X, y = w["X"], w["y"]
-    t0 = time.perf_counter()
-    ranks, nu = oracle.encode(X[:n_try])
-    oracle.de_run(ranks, nu, y[:n_try], w["K"], depth=D, P=P, G=1, seed=0)
-    dt = time.perf_counter() - t0
-    n_s = int(min(len(X), max(n_try, n_try * budget_s / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    ranks, nu = oracle.encode(X[:n_s])
-    oracle.de_run(ranks, nu, y[:n_s], w["K"], depth=D, P=P, G=1, seed=0)
-    dt = time.perf_counter() - t0
+    cores = oracle.host_cores()
+    old = oracle.set_threads(cores)
+    try:
+        P, D = w["pop"], w["depth"]
+        X, y = w["X"], w["y"]
+        n_try = min(len(X), 20_000 * cores)
+        t0 = time.perf_counter()
+        _oracle_step(X[:n_try], y[:n_try], w["K"], P, D, 0)
+        dt = time.perf_counter() - t0
+        n_s = int(min(len(X), max(n_try, n_try * budget_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        _oracle_step(X[:n_s], y[:n_s], w["K"], P, D, 0)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(old)
     evals = 2 * P * n_s
-    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d samples of the workload: rank encode + initial evaluation + 1 DE "
-                      "generation of the P=1024 depth-4 population (%d evals, %.1f s)" % (n_s, evals, dt)}
+                      "generation of the P=1024 depth-4 population (%d evals, %.1f s), oracle's "
+                      "OpenMP twins on %d threads" % (n_s, evals, dt, cores)}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, rank 0 only, on bounded samples of the workload."""
+    """Reference arm: the CPU oracle on the host's cores, rank 0 only, on bounded samples of
+    the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     from paper_2311_06952_gb300 import datagen
     w = dict(WORKLOAD)
-    n_s = 40_000
+    cores = oracle.host_cores()
+    n_s = min(w["n"], 40_000 * cores)
     full = datagen.make_workload(3, n=n_s)
     P, D = w["pop"], w["depth"]
     times = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        ranks, nu = oracle.encode(full["X"])
-        oracle.de_run(ranks, nu, full["y"], full["K"], depth=D, P=P, G=1, seed=it)
-        dt = time.perf_counter() - t0
-        if it >= args.warmup:
-            times.append(dt)
+    old = oracle.set_threads(cores)
+    try:
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            _oracle_step(full["X"], full["y"], full["K"], P, D, it)
+            dt = time.perf_counter() - t0
+            if it >= args.warmup:
+                times.append(dt)
+    finally:
+        oracle.set_threads(old)
     evals = 2 * P * n_s
     ms = 1000.0 * float(np.mean(times))
     value = evals / (ms / 1000.0)
@@ -220,8 +238,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(w, sample="each step: first %d samples, rank encode + initial evaluation "
                                      "+ 1 DE generation (P=1024, depth 4)" % n_s),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d samples x 1024 trees x 2 evaluations per step" % n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d samples x 1024 trees x 2 evaluations per step, oracle's "
+                                       "OpenMP twins on %d threads" % (n_s, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -607,8 +626,10 @@ def run_ours(args):
     for i in range(args.warmup):
         step(multirank.stream_id(rank))
     torch.cuda.synchronize()
+    # the timed loop runs the path as a user gets it: per-launch timing off, so every DEOCT
+    # generation is one replay of the captured CUDA graph
     ctx.reset_stats()
-    ctx.set_timing(True)
+    ctx.set_timing(False)
     clk = ClockSampler(local) if rank == 0 else None
     if clk:
         clk.start()
@@ -625,10 +646,23 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     clocks = clk.stop() if clk else None
     st = ctx.stats()
-    ctx.set_timing(False)
     ms_total = multirank.max_over_ranks(ms_total, world, "cuda")
     ms_step = ms_total / args.steps
     value = multirank.whole_job_rate(evals_per_step, world, ms_step / 1000.0)
+
+    # ---- roofline pass: one more step with library-side CUDA events around every evaluator
+    # launch (the launches are then issued directly, not replayed from a graph) ---------------
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    step(multirank.stream_id(rank))
+    f1.record(stream)
+    torch.cuda.synchronize()
+    st_roof = ctx.stats()
+    ctx.set_timing(False)
+    ms_step_timed_launches = f0.elapsed_time(f1)
 
     # ---- end to end through the public API, host buffers ----------------------
     Xh = torch.from_numpy(data["X"]).pin_memory()
@@ -657,7 +691,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     peaks, peak_kind = _peaks()
-    eval_ms = st["eval_ms"] / max(1, st["eval_timed"])
+    eval_ms = st_roof["eval_ms"] / max(1, st_roof["eval_timed"])
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     # per tree-sample evaluation, per level: load the node's feature and threshold, load the
     # sample's rank, compare, step to the child; then the count increment (2)
@@ -680,7 +714,11 @@ def run_ours(args):
                          _traffic_default() if args.n == WORKLOAD["n"] else None),
                      "kernel": "eval_kernel<2,4,0> (population evaluator)",
                      "ops_per_launch": ops_per_launch, "ops_per_eval": ops_per_eval,
-                     "launch_ms": eval_ms,
+                     "launch_ms": eval_ms, "launches_timed": int(st_roof["eval_timed"]),
+                     "timing_pass": "one extra step after the timed loop, launches issued directly "
+                                    "with CUDA events around each evaluator launch (%.1f ms for the "
+                                    "step vs %.1f ms per graph-replayed step in the timed loop)"
+                                    % (ms_step_timed_launches, ms_step),
                      "strict_view": {"ops_per_eval": 2 * D + 1, "ops_per_launch": strict_ops,
                                      "achieved": strict_ops / (eval_ms / 1000.0) / 1e12,
                                      "frac": strict_ops / (eval_ms / 1000.0) / 1e12 / peak},

@@ -162,6 +162,19 @@ DEOCT_API int deoct_encode_ex(deoct_ctx* ctx, const float* X, int64_t n, int32_t
                               int32_t rank_bytes, void* ranks_out, int64_t ld,
                               uint32_t* n_unique_out, float* unique_out, void* stream);
 
+/* As deoct_encode_ex with the rank width chosen from the data: uint16 ranks
+ * when every n_p <= 65536 (Section 3.1's threshold sets then fit 16 bits),
+ * else uint32, written as [F][ld] of that width.  The width is decided from n_p
+ * after the sort, before any rank is written, so no second pass is needed.
+ *  ranks_out      device buffer of at least F * ld * 4 bytes (room for either width)
+ *  ld             row stride in elements of the chosen width; >= n and a
+ *                 multiple of 8 (rows stay 16-byte aligned at either width)
+ *  rank_bytes_out host int32: 2 or 4, the width written
+ * sync. */
+DEOCT_API int deoct_encode_auto(deoct_ctx* ctx, const float* X, int64_t n, int32_t F,
+                                void* ranks_out, int64_t ld, uint32_t* n_unique_out,
+                                float* unique_out, int32_t* rank_bytes_out, void* stream);
+
 /* ---- a2: decoding (Eq. aenc, Eq. benc) ------------------------------------
  * genes [P][2B] float32, individual s_r = [ahat_1..ahat_B, bhat_1..bhat_B],
  * B = 2^depth - 1.  a_t = floor(ahat_t) clamped to {0..F} (0 = no split);
@@ -300,16 +313,23 @@ DEOCT_API int deoct_predict(deoct_ctx* ctx, const float* X, int64_t m, int32_t F
  * bytes inside the library, resident on every GPU that loads the library until
  * the process exits.
  *  - Runs on the current CUDA device.  The first call on a device looks up the
- *    array's device address (cudaGetSymbolAddress); make that first call before
- *    any stream capture.
+ *    array's device address (cudaGetSymbolAddress) and keeps it for the life of
+ *    the process; make that first call before any stream capture.  The kept
+ *    address does not survive cudaDeviceReset: a process that resets a device
+ *    must not call this entry point on it afterwards.
  *  - Requests needing more scratch than the array holds (P * (2^depth - 1) * 4
  *    bytes of trees, plus P * 2^depth * K * 4 bytes of counts when counts_out is
- *    NULL, plus 256) return DEOCT_ERR_INVALID before any GPU work.
+ *    NULL, plus 256) return DEOCT_ERR_INVALID before any GPU work, and so does
+ *    P outside 1..262144 (the limit of deoct_eval_population).
  *  - Every call shares the one array and each call clears what must start at
  *    zero; calls whose GPU work overlaps (other streams, other threads) race on
  *    it and must be serialised by the caller.
- *  - Trees naming a feature > F route right; with no context there is no later
- *    sync call to report it.
+ *  - Device-side errors -- a tree naming a feature > F (it routes right), a
+ *    sample_idx entry outside 0..n-1 (read as sample 0), a bounded device wait
+ *    that expired -- cannot be returned by a later sync call, as there is no
+ *    context.  Instead every errors_out entry of that call is set to 0xFFFFFFFF
+ *    (no true error count reaches it, since n <= 2^24) and counts_out is not to
+ *    be trusted.  With errors_out NULL such errors go unreported.
  * Arguments as deoct_eval_population.  async. */
 #define DEOCT_NOALLOC_SCRATCH_BYTES (8u << 20)
 DEOCT_API int deoct_eval_population_noalloc(const deoct_dataset* ds, const int32_t* sample_idx,

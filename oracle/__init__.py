@@ -8,7 +8,10 @@ from there: the two share no code.  Inputs come from the seeded generators in
 passed in by the caller.
 
 The arithmetic lives in ``deoct_oracle.c`` (plain single-threaded C, built with
-``-O2 -ffp-contract=off``); this module only marshals numpy arrays into it.
+``-O2 -ffp-contract=off``); this module only marshals numpy arrays into it.  Its
+OpenMP twins (``encode_omp``, ``eval_counts_omp``, and the counting inside
+``de_run`` / ``mh`` after ``set_threads(n > 1)``) compute the same integers on
+several host cores; tests pin them bit for bit to the plain functions.
 Each wrapper names the paper passage its C function follows.
 
 Parity status per function (see the tests under ``tests/test_oracle_*.py``):
@@ -50,7 +53,10 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-Wall",
                "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
+        # the OpenMP twins (timing, full-size checks); without OpenMP they run on one thread
+        r = subprocess.run(cmd[:-3] + ["-fopenmp"] + cmd[-3:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -98,6 +104,49 @@ def encode(X):
     if rc != ORC_OK:
         raise ValueError("oracle encode failed: %d" % rc)
     return ranks, nu
+
+
+def set_threads(n):
+    """Threads of the OpenMP twins (encode_omp, eval_counts_omp, and the counting inside
+    de_run / mh); 1 restores the plain loops.  Returns the previous setting."""
+    return int(lib().orc_set_threads(ctypes.c_int(int(n))))
+
+
+def host_cores():
+    """Cores this process may run on (the thread count the timed oracle uses)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def encode_omp(X):
+    """encode() with the features spread over the set_threads() threads (same result)."""
+    X = _c(X, np.float32)
+    n, F = X.shape
+    ranks = np.empty((F, n), np.uint32)
+    nu = np.empty(F, np.uint32)
+    rc = lib().orc_encode_omp(_p(X), ctypes.c_int64(n), ctypes.c_int32(F), _p(ranks), _p(nu))
+    if rc != ORC_OK:
+        raise ValueError("oracle encode failed: %d" % rc)
+    return ranks, nu
+
+
+def eval_counts_omp(ranks, y, K, a, theta, depth, idx=None):
+    """eval_counts() with (tree, sample chunk) work spread over the set_threads() threads."""
+    ranks = _c(ranks, np.uint32)
+    y = _c(y, np.uint8)
+    a = _c(a, np.int32)
+    theta = _c(theta, np.uint32)
+    F, n = ranks.shape
+    P = a.shape[0]
+    counts = np.empty((P, 1 << depth, K), np.uint32)
+    idx_arr = None if idx is None else _c(idx, np.int32)
+    n_sub = n if idx is None else len(idx_arr)
+    lib().orc_eval_counts_omp(_p(ranks), ctypes.c_int64(n), ctypes.c_int32(F), _p(y), ctypes.c_int32(K),
+                              _p(idx_arr), ctypes.c_int64(n_sub), _p(a), _p(theta),
+                              ctypes.c_int32(P), ctypes.c_int32(depth), _p(counts))
+    return counts
 
 
 def philox(counter, key):

@@ -33,6 +33,12 @@
 #define ORC_ERR_INVALID (-1)
 #define ORC_ERR_OOM (-2)
 
+/* Threads of the OpenMP twins at the end of this file (1 = the plain loops). */
+static int g_threads = 1;
+void orc_eval_counts_omp(const uint32_t* ranks, int64_t n, int32_t F, const uint8_t* y,
+                         int32_t K, const int32_t* idx, int64_t n_sub, const int32_t* a,
+                         const uint32_t* theta, int32_t P, int32_t depth, uint32_t* counts);
+
 /* ------------------------------------------------------------------------- */
 /* Threshold sets as ranks (Section 3.1, "Decoding Tree Candidates").          */
 /* ------------------------------------------------------------------------- */
@@ -49,38 +55,44 @@ static int cmp_float(const void* pa, const void* pb) {
  * Ranks are taken on the raw float32 values (Reading C2: monotone min-max
  * scaling does not change them); -0.0 is the same value as +0.0.
  * X is [n][F] row-major; ranks_out is [F][n]; returns ORC_ERR_INVALID on NaN. */
+static int encode_feature(const float* X, int64_t n, int32_t F, int32_t p, float* col, float* uniq,
+                          uint32_t* ranks_out, uint32_t* n_unique_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    float v = X[i * F + p];
+    if (isnan(v)) return ORC_ERR_INVALID;
+    if (v == 0.0f) v = 0.0f; /* -0.0 and +0.0 are one value */
+    col[i] = v;
+  }
+  memcpy(uniq, col, (size_t)n * sizeof(float));
+  qsort(uniq, (size_t)n, sizeof(float), cmp_float);
+  int64_t np = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (np == 0 || uniq[i] != uniq[np - 1]) uniq[np++] = uniq[i];
+  n_unique_out[p] = (uint32_t)np;
+  for (int64_t i = 0; i < n; ++i) {
+    /* lower_bound: number of unique values strictly below col[i] */
+    int64_t lo = 0, hi = np;
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (uniq[mid] < col[i]) lo = mid + 1; else hi = mid;
+    }
+    ranks_out[(int64_t)p * n + i] = (uint32_t)lo;
+  }
+  return ORC_OK;
+}
+
 int orc_encode(const float* X, int64_t n, int32_t F, uint32_t* ranks_out,
                uint32_t* n_unique_out) {
   if (n <= 0 || F <= 0) return ORC_ERR_INVALID;
   float* col = (float*)malloc((size_t)n * sizeof(float));
   float* uniq = (float*)malloc((size_t)n * sizeof(float));
   if (!col || !uniq) { free(col); free(uniq); return ORC_ERR_OOM; }
-  for (int32_t p = 0; p < F; ++p) {
-    for (int64_t i = 0; i < n; ++i) {
-      float v = X[i * F + p];
-      if (isnan(v)) { free(col); free(uniq); return ORC_ERR_INVALID; }
-      if (v == 0.0f) v = 0.0f; /* -0.0 and +0.0 are one value */
-      col[i] = v;
-    }
-    memcpy(uniq, col, (size_t)n * sizeof(float));
-    qsort(uniq, (size_t)n, sizeof(float), cmp_float);
-    int64_t np = 0;
-    for (int64_t i = 0; i < n; ++i)
-      if (np == 0 || uniq[i] != uniq[np - 1]) uniq[np++] = uniq[i];
-    n_unique_out[p] = (uint32_t)np;
-    for (int64_t i = 0; i < n; ++i) {
-      /* lower_bound: number of unique values strictly below col[i] */
-      int64_t lo = 0, hi = np;
-      while (lo < hi) {
-        int64_t mid = lo + (hi - lo) / 2;
-        if (uniq[mid] < col[i]) lo = mid + 1; else hi = mid;
-      }
-      ranks_out[(int64_t)p * n + i] = (uint32_t)lo;
-    }
-  }
+  int rc = ORC_OK;
+  for (int32_t p = 0; p < F && rc == ORC_OK; ++p)
+    rc = encode_feature(X, n, F, p, col, uniq, ranks_out, n_unique_out);
   free(col);
   free(uniq);
-  return ORC_OK;
+  return rc;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -288,7 +300,10 @@ static void eval_genes(const float* genes, int32_t P, const orc_de_params* prm,
                        const uint8_t* y, int32_t K, const int32_t* idx, int64_t n_sub,
                        int32_t* a, uint32_t* theta, uint32_t* counts, double* fit) {
   orc_decode(genes, P, prm->depth, F, n_unique, a, theta);
-  orc_eval_counts(ranks, n, F, y, K, idx, n_sub, a, theta, P, prm->depth, counts);
+  if (g_threads > 1)
+    orc_eval_counts_omp(ranks, n, F, y, K, idx, n_sub, a, theta, P, prm->depth, counts);
+  else
+    orc_eval_counts(ranks, n, F, y, K, idx, n_sub, a, theta, P, prm->depth, counts);
   orc_fitness(counts, a, P, prm->depth, K, idx ? n_sub : n, prm->n_min, prm->alpha, fit,
               NULL, NULL, NULL);
 }
@@ -685,7 +700,8 @@ int orc_mh(const uint32_t* ranks, int64_t n, int32_t F, const uint32_t* n_unique
     uint32_t* counts = (uint32_t*)malloc((size_t)L * K * sizeof(uint32_t));
     if (!counts) rc = ORC_ERR_OOM;
     else {
-      orc_eval_counts(ranks, n, F, y, K, NULL, n, a_out, theta_out, 1, D, counts);
+      if (g_threads > 1) orc_eval_counts_omp(ranks, n, F, y, K, NULL, n, a_out, theta_out, 1, D, counts);
+      else orc_eval_counts(ranks, n, F, y, K, NULL, n, a_out, theta_out, 1, D, counts);
       orc_leaf_classes(counts, 1, D, K, leaf_class_out);
       free(counts);
     }
@@ -741,5 +757,86 @@ void orc_predict(const float* X, int64_t m, int32_t F, const int32_t* a, const d
       t = left ? 2 * t : 2 * t + 1;
     }
     pred[i] = leaf_class[t - (B + 1)];
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* OpenMP twins for timing and for checking full-size workloads.  They compute */
+/* exactly what the plain functions above compute (integer counts and sorts,   */
+/* independent per feature or per (tree, sample chunk)), and tests check them  */
+/* bit for bit against those functions.  With g_threads = 1 nothing here runs. */
+/* ------------------------------------------------------------------------- */
+
+/* Threads used by orc_encode_omp, orc_eval_counts_omp and, through them, by
+ * orc_de_run and orc_mh (n < 1 means 1).  Returns the previous setting. */
+int orc_set_threads(int n) {
+  int old = g_threads;
+  g_threads = n < 1 ? 1 : n;
+  return old;
+}
+
+/* orc_encode with the features spread over the threads. */
+int orc_encode_omp(const float* X, int64_t n, int32_t F, uint32_t* ranks_out,
+                   uint32_t* n_unique_out) {
+  if (n <= 0 || F <= 0) return ORC_ERR_INVALID;
+  int rc = ORC_OK;
+#pragma omp parallel num_threads(g_threads)
+  {
+    float* col = (float*)malloc((size_t)n * sizeof(float));
+    float* uniq = (float*)malloc((size_t)n * sizeof(float));
+    int mine = (col && uniq) ? ORC_OK : ORC_ERR_OOM;
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t p = 0; p < F; ++p)
+      if (mine == ORC_OK) mine = encode_feature(X, n, F, p, col, uniq, ranks_out, n_unique_out);
+    free(col);
+    free(uniq);
+#pragma omp critical
+    if (mine != ORC_OK && rc == ORC_OK) rc = mine;
+  }
+  return rc;
+}
+
+/* orc_eval_counts with the (tree, chunk of 2^16 samples) pairs spread over the
+ * threads: each pair counts into its own zeroed array, added to counts[r]. */
+void orc_eval_counts_omp(const uint32_t* ranks, int64_t n, int32_t F, const uint8_t* y,
+                         int32_t K, const int32_t* idx, int64_t n_sub, const int32_t* a,
+                         const uint32_t* theta, int32_t P, int32_t depth, uint32_t* counts) {
+  (void)F;
+  const int32_t B = (1 << depth) - 1, L = 1 << depth;
+  const int64_t LK = (int64_t)L * K, CH = (int64_t)1 << 16;
+  memset(counts, 0, (size_t)P * LK * sizeof(uint32_t));
+  const int64_t m = idx ? n_sub : n;
+  const int64_t nch = (m + CH - 1) / CH, items = (int64_t)P * nch;
+  if (items == 0) return;
+#pragma omp parallel num_threads(g_threads)
+  {
+    uint32_t* loc = (uint32_t*)malloc((size_t)LK * sizeof(uint32_t));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t it = 0; it < items; ++it) {
+      const int32_t r = (int32_t)(it / nch);
+      const int64_t j0 = (it % nch) * CH, j1 = j0 + CH < m ? j0 + CH : m;
+      const int32_t* ar = a + (int64_t)r * B;
+      const uint32_t* tr = theta + (int64_t)r * B;
+      if (loc) {
+        memset(loc, 0, (size_t)LK * sizeof(uint32_t));
+        for (int64_t j = j0; j < j1; ++j) {
+          int64_t i = idx ? idx[j] : j;
+          loc[(int64_t)route(ranks, n, i, ar, tr, depth) * K + y[i]] += 1;
+        }
+        for (int64_t e = 0; e < LK; ++e)
+          if (loc[e]) {
+#pragma omp atomic
+            counts[(int64_t)r * LK + e] += loc[e];
+          }
+      } else {
+        for (int64_t j = j0; j < j1; ++j) {
+          int64_t i = idx ? idx[j] : j;
+          int64_t e = (int64_t)r * LK + (int64_t)route(ranks, n, i, ar, tr, depth) * K + y[i];
+#pragma omp atomic
+          counts[e] += 1;
+        }
+      }
+    }
+    free(loc);
   }
 }

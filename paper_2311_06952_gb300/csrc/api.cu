@@ -111,9 +111,10 @@ static int validate_params(const deoct_params* p, bool need_pop) {
   return DEOCT_OK;
 }
 
-static EvalProb single_prob(const deoct_dataset* ds, const int32_t* idx, int64_t n_sub,
-                            const uint32_t* nodes, uint32_t* counts, int P) {
-  EvalProb p;
+EvalPlan single_eval_plan(const deoct_dataset* ds, const int32_t* idx, int64_t n_sub,
+                          const uint32_t* nodes, uint32_t* counts, int P, const EvalConfig& cfg) {
+  EvalPlan plan;
+  EvalProb& p = plan.single;
   p.ranks = ds->ranks;
   p.labels = ds->labels;
   p.idx = idx;
@@ -130,7 +131,12 @@ static EvalProb single_prob(const deoct_dataset* ds, const int32_t* idx, int64_t
                        ((ds->ld * ds->rank_bytes) % 16 == 0);
   p.tma = (idx == nullptr && aligned) ? 1 : 0;
   p.lab_tma = (p.tma && reinterpret_cast<uintptr_t>(ds->labels) % 16 == 0) ? 1 : 0;
-  return p;
+  plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
+  plan.Fmax = ds->F;
+  plan.Kmax = ds->K;
+  plan.Pmax = P;
+  plan.max_count = n_sub;
+  return plan;
 }
 
 // evaluate one population on one (sub)set: counts must be zero beforehand
@@ -139,13 +145,7 @@ static int eval_single(deoct_ctx* ctx, const deoct_dataset* ds, const int32_t* i
                        cudaStream_t s) {
   if (n_sub == 0) return DEOCT_OK;
   EvalConfig cfg = eval_choose_config(ctx, ds->rank_bytes, depth, ds->F, ds->K, P, n_sub, 1);
-  EvalPlan plan;
-  plan.single = single_prob(ds, idx, n_sub, nodes, counts, P);
-  plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
-  plan.Fmax = ds->F;
-  plan.Kmax = ds->K;
-  plan.Pmax = P;
-  plan.max_count = n_sub;
+  EvalPlan plan = single_eval_plan(ds, idx, n_sub, nodes, counts, P, cfg);
   return eval_launch(ctx, ds->rank_bytes, depth, plan, cfg, s);
 }
 
@@ -164,15 +164,9 @@ static int eval_single_fused(deoct_ctx* ctx, const deoct_dataset* ds, const int3
   DEOCT_TRY(scratch_get(ctx, SL_EVAL_ACC, bytes, (void**)&base));
   if (grows) DEOCT_CUDA_TRY(cudaMemsetAsync(base, 0, ctx->scratch[SL_EVAL_ACC].bytes, s));
   EvalConfig cfg = eval_choose_config(ctx, ds->rank_bytes, depth, ds->F, ds->K, P, n_sub, 1);
-  EvalPlan plan;
-  plan.single = single_prob(ds, idx, n_sub, nullptr, base + 4, P);
+  EvalPlan plan = single_eval_plan(ds, idx, n_sub, nullptr, base + 4, P, cfg);
   plan.single.a16 = a;
   plan.single.th32 = theta;
-  plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
-  plan.Fmax = ds->F;
-  plan.Kmax = ds->K;
-  plan.Pmax = P;
-  plan.max_count = n_sub;
   plan.ticket = base;
   plan.counts_out = counts_out;
   plan.errors_out = errors_out;
@@ -214,7 +208,9 @@ static DEArgs de_args(const deoct_dataset* ds, const deoct_params* p, int64_t n_
   d.n_unique = ds->n_unique;
   d.seeds = seeds;
   d.n_valid = n_sub;
+  d.seed = p->seed;
   d.stream_id = stream_id;
+  d.G = p->gens;
   d.S = S;
   d.F = ds->F;
   d.K = ds->K;
@@ -227,8 +223,6 @@ static DEArgs de_args(const deoct_dataset* ds, const deoct_params* p, int64_t n_
   a.alpha = p->alpha;
   a.n_min = p->n_min;
   a.dither = (p->flags & DEOCT_DITHER_M) ? 1 : 0;
-  a.G = p->gens;
-  a.seed = p->seed;
   a.status = status;
   return a;
 }
@@ -479,6 +473,25 @@ int deoct_encode_ex(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, int32_
         return set_error(DEOCT_ERR_INVALID, "feature %d has %u distinct values: needs rank_bytes = 4",
                          f, h[f]);
   }
+  return DEOCT_OK;
+  API_END
+}
+
+int deoct_encode_auto(deoct_ctx* ctx, const float* X, int64_t n, int32_t F, void* ranks_out,
+                      int64_t ld, uint32_t* n_unique_out, float* unique_out,
+                      int32_t* rank_bytes_out, void* stream) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!X || !ranks_out || !n_unique_out || !rank_bytes_out)
+    return set_error(DEOCT_ERR_INVALID, "NULL pointer");
+  if (n < 1 || n > kMaxN) return set_error(DEOCT_ERR_INVALID, "n = %lld outside 1..2^24", (long long)n);
+  if (F < 1 || F > kMaxF) return set_error(DEOCT_ERR_INVALID, "F = %d outside 1..256", F);
+  if (ld < n || ld % 8 != 0) return set_error(DEOCT_ERR_INVALID, "ld must be >= n and a multiple of 8");
+  int W = 0;
+  DEOCT_TRY(encode_run(ctx, X, n, F, 0, ranks_out, ld, n_unique_out, unique_out, s, &W));
+  DEOCT_TRY(check_status(ctx, s));
+  *rank_bytes_out = W;
   return DEOCT_OK;
   API_END
 }

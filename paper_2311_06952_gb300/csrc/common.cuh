@@ -53,6 +53,9 @@ constexpr int64_t kMaxN = int64_t(1) << 24;
 constexpr int kMinPop = 4;
 constexpr int kMaxPop = 4096;
 constexpr uint32_t kThetaMask = 0x00FFFFFFu;
+// error count written when a device status bit says the class counts are not to be
+// trusted (no true count reaches it: n <= 2^24)
+constexpr uint32_t kErrorsInvalid = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------------------
 // context

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
     } else {
       U64x4 blk;
       for (int q = 0; q < m; ++q) {
-        if ((q & 7) == 0) blk = philox4x64_10(0ull, (uint64_t)r, (uint64_t)(q >> 3), 0ull, a.seed,
+        if ((q & 7) == 0) blk = philox4x64_10(0ull, (uint64_t)r, (uint64_t)(q >> 3), 0ull, pb.seed,
                                               pb.stream_id);
         const float u = u01(draw_from_block(blk, (uint32_t)q));
         const bool is_a = q < B;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
 
   if (!(flags & DE_TRIAL)) return;
   const int g = g_s;
-  if (g < 1 || g > a.G) return;  // device-driven replay past the last generation
+  if (g < 1 || g > pb.G) return;  // device-driven replay past the last generation
   const int best = best_s;
   const float ub_a = (float)(pb.F + 1);
   const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   const int per = (m + G - 1) / G;  // consecutive genes per lane: they share Philox blocks
   for (int r = r0; r < P; r += rstep) {
     // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
-    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, a.seed, pb.stream_id);
+    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, pb.seed, pb.stream_id);
     const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
     const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
     int r1 = (int)below(x0, (uint32_t)(P - 1));
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
       const uint32_t s = 4u + (uint32_t)q;
       if ((s >> 3) != cur) {
         cur = s >> 3;
-        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, a.seed, pb.stream_id);
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, pb.seed, pb.stream_id);
       }
       const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
       const float vc = clamp_gene(v, q < B ? hi_a : hi_b);

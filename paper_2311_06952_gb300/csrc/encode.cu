@@ -270,7 +270,7 @@ int radix_sort_segments(deoct_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1
 }
 
 int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ranks_out,
-               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s) {
+               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s, int* W_used) {
   const size_t elems = (size_t)n * F;
   uint32_t *k0, *k1, *v0, *v1, *C;
   DEOCT_TRY(scratch_get(ctx, SL_ENC_K0, elems * 4, (void**)&k0));
@@ -290,6 +290,18 @@ int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ra
   dim3 g(ntiles, F);
   rank_count_kernel<<<g, kThreads, 0, s>>>(ks, n, ntiles, C);
   rank_scan_kernel<<<F, kThreads, 0, s>>>(C, ntiles, n_unique_out);
+  if (W == 0) {
+    // automatic width: n_p is known once the flags are scanned, before any rank is written
+    DEOCT_TRY(check_launch("rank count / scan kernels"));
+    uint32_t* h = nullptr;
+    DEOCT_TRY(pinned_get(ctx, sizeof(uint32_t) * F, (void**)&h));
+    DEOCT_CUDA_TRY(cudaMemcpyAsync(h, n_unique_out, sizeof(uint32_t) * F, cudaMemcpyDeviceToHost, s));
+    DEOCT_CUDA_TRY(cudaStreamSynchronize(s));
+    uint32_t mx = 0;
+    for (int f = 0; f < F; ++f) mx = h[f] > mx ? h[f] : mx;
+    W = mx <= 65536u ? 2 : 4;
+  }
+  if (W_used) *W_used = W;
   if (W == 2)
     rank_scatter_kernel<uint16_t><<<g, kThreads, 0, s>>>(ks, vs, n, ntiles, C,
                                                         static_cast<uint16_t*>(ranks_out), ld,

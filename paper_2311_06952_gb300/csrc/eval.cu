@@ -258,9 +258,14 @@ int dispatch_depth(deoct_ctx* ctx, int D, int mode, int Q, const EvalArgs& args,
 }
 
 __global__ void errors_kernel(const uint32_t* __restrict__ counts, int P, int L, int K,
-                              int64_t n_valid, uint32_t* __restrict__ errors) {
+                              int64_t n_valid, uint32_t* __restrict__ errors,
+                              const int* __restrict__ status) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= P) return;
+  if (status != nullptr && *status != 0) {  // the counts are not to be trusted
+    errors[r] = kErrorsInvalid;
+    return;
+  }
   const uint32_t* c = counts + (int64_t)r * L * K;
   int64_t correct = 0;
   for (int l = 0; l < L; ++l) {
@@ -542,8 +547,8 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
 }
 
 int launch_errors(deoct_ctx* ctx, const uint32_t* counts, int P, int L, int K, int64_t n_valid,
-                  uint32_t* errors, cudaStream_t stream) {
-  errors_kernel<<<(P + 127) / 128, 128, 0, stream>>>(counts, P, L, K, n_valid, errors);
+                  uint32_t* errors, cudaStream_t stream, const int* status) {
+  errors_kernel<<<(P + 127) / 128, 128, 0, stream>>>(counts, P, L, K, n_valid, errors, status);
   count_launch(ctx);
   return check_launch("errors_kernel");
 }

@@ -75,9 +75,16 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
 // build the job list for host-side problems (tile counts per problem)
 void eval_build_jobs(const std::vector<int64_t>& counts, const std::vector<int>& pops, int S,
                      int TG, std::vector<EvalJob>* jobs, int64_t* total_tiles);
-// errors[r] = n_valid - sum_leaf max_k counts (the loss identity of Section 2)
+// errors[r] = n_valid - sum_leaf max_k counts (the loss identity of Section 2); with a
+// non-null device status word that is non-zero when the kernel runs, every errors[r] is
+// kErrorsInvalid instead
 int launch_errors(deoct_ctx* ctx, const uint32_t* counts, int P, int L, int K, int64_t n_valid,
-                  uint32_t* errors, cudaStream_t stream);
+                  uint32_t* errors, cudaStream_t stream, const int* status = nullptr);
+// The evaluator plan of one population on one (sub)set of a dataset, for the shape `cfg`:
+// rank rows and labels are staged by bulk copies when the set is the whole dataset and the
+// rows are 16-byte aligned (ranks base and row stride), else gathered with plain loads.
+EvalPlan single_eval_plan(const deoct_dataset* ds, const int32_t* idx, int64_t n_sub,
+                          const uint32_t* nodes, uint32_t* counts, int P, const EvalConfig& cfg);
 // pack decoded (a, theta) into evaluator nodes, flagging a > F
 int launch_pack_nodes(deoct_ctx* ctx, const uint16_t* a, const uint32_t* theta, int64_t count,
                       int F, uint32_t* nodes, cudaStream_t stream);
@@ -97,9 +104,13 @@ struct DEProb {
   const uint32_t* n_unique;
   const float* seeds;    // [S][2B] or nullptr
   int64_t n_valid;
+  uint64_t seed;         // Philox key (seed, stream_id) of this problem's draws
   uint64_t stream_id;
-  int32_t S, F, K, pad;
+  int32_t S, F, K;
+  int32_t G;             // generations of this problem: trials are built for g <= G
 };
+// One DE launch: problems that share P, depth and the DE constants (each
+// problem keeps its own data, Philox key and generation count).
 struct DEArgs {
   DEProb single;
   const DEProb* probs;   // nullptr: use `single`
@@ -107,8 +118,7 @@ struct DEArgs {
   int P, depth;
   float M, CR;
   double alpha;
-  int n_min, dither, G;
-  uint64_t seed;
+  int n_min, dither;
   int* status;
 };
 enum : int { DE_FIRST = 1, DE_SELECT = 2, DE_TRIAL = 4, DE_GEN_DEVICE = 8 };
@@ -130,8 +140,11 @@ int launch_decode(deoct_ctx* ctx, const float* genes, int P, int depth, int F,
 // ---------------------------------------------------------------------------
 // encoder (encode.cu)
 // ---------------------------------------------------------------------------
+// W = 2 or 4; W = 0 picks 2 when every n_p <= 65536, else 4 (reads n_p back: syncs s)
+// and reports the width used in *W_used (nullable)
 int encode_run(deoct_ctx* ctx, const float* X, int64_t n, int F, int W, void* ranks_out,
-               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s);
+               int64_t ld, uint32_t* n_unique_out, float* unique_out, cudaStream_t s,
+               int* W_used = nullptr);
 
 // ---------------------------------------------------------------------------
 // prediction (predict.cu)

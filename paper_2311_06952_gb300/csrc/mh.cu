@@ -524,7 +524,9 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     d.n_unique = ds->n_unique;
     d.seeds = (d_seeds && S > 0) ? d_seeds + (size_t)m * S * m2 : nullptr;
     d.n_valid = c.counts[m];
+    d.seed = prm->seed;
     d.stream_id = (uint64_t)node_ids[m];
+    d.G = prm->gens;
     d.S = d.seeds ? S : 0;
     d.F = F;
     d.K = K;
@@ -560,8 +562,6 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   a.alpha = prm->alpha;
   a.n_min = prm->n_min;
   a.dither = (prm->flags & DEOCT_DITHER_M) ? 1 : 0;
-  a.G = prm->gens;
-  a.seed = prm->seed;
   a.status = ctx->d_status;
   DEOCT_TRY(de_launch_init(ctx, a, s));
 

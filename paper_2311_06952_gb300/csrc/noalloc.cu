@@ -65,7 +65,7 @@ extern "C" DEOCT_API int deoct_eval_population_noalloc(const deoct_dataset* ds,
       return set_error(DEOCT_ERR_INVALID, "without sample_idx n_sub must equal n");
     if (n_sub < 0 || n_sub > kMaxN) return set_error(DEOCT_ERR_INVALID, "n_sub out of range");
     if (!a || !theta) return set_error(DEOCT_ERR_INVALID, "NULL tree arrays");
-    if (P < 1) return set_error(DEOCT_ERR_INVALID, "P = %d out of range", P);
+    if (P < 1 || P > kMaxPop * 64) return set_error(DEOCT_ERR_INVALID, "P = %d out of range", P);
     if (depth < 1 || depth > kMaxDepth) return set_error(DEOCT_ERR_INVALID, "depth out of range");
     const size_t B = ((size_t)1 << depth) - 1, L = (size_t)1 << depth;
     const size_t nodes_bytes = (size_t)P * B * 4;
@@ -98,33 +98,14 @@ extern "C" DEOCT_API int deoct_eval_population_noalloc(const deoct_dataset* ds,
     DEOCT_TRY(launch_pack_nodes(&ctx, a, theta, (int64_t)P * B, ds->F, nodes, s));
     if (n_sub > 0) {
       EvalConfig cfg = eval_choose_config(&ctx, ds->rank_bytes, depth, ds->F, ds->K, P, n_sub, 1);
-      EvalPlan plan;
-      EvalProb& p = plan.single;
-      p.ranks = ds->ranks;
-      p.labels = ds->labels;
-      p.idx = sample_idx;
-      p.nodes = nodes;
-      p.counts = counts;
-      p.ld = ds->ld;
-      p.ncols = ds->n;
-      p.start = 0;
-      p.count = n_sub;
-      p.F = ds->F;
-      p.K = ds->K;
-      p.P = P;
-      const bool aligned = (reinterpret_cast<uintptr_t>(ds->ranks) % 16 == 0) &&
-                           ((ds->ld * ds->rank_bytes) % 16 == 0);
-      p.tma = (sample_idx == nullptr && aligned) ? 1 : 0;
-      p.lab_tma = (p.tma && reinterpret_cast<uintptr_t>(ds->labels) % 16 == 0) ? 1 : 0;
-      plan.total_tiles = ((n_sub + cfg.S - 1) / cfg.S) * (int64_t)((P + cfg.TG - 1) / cfg.TG);
-      plan.Fmax = ds->F;
-      plan.Kmax = ds->K;
-      plan.Pmax = P;
-      plan.max_count = n_sub;
+      EvalPlan plan = single_eval_plan(ds, sample_idx, n_sub, nodes, counts, P, cfg);
       DEOCT_TRY(eval_launch(&ctx, ds->rank_bytes, depth, plan, cfg, s));
     }
+    // no later sync call can report the status word: a set bit (a tree naming a feature
+    // > F, a sample index out of range, an expired bounded wait) turns every error count
+    // into kErrorsInvalid, read on the device
     if (errors_out)
-      DEOCT_TRY(launch_errors(&ctx, counts, P, (int)L, ds->K, n_sub, errors_out, s));
+      DEOCT_TRY(launch_errors(&ctx, counts, P, (int)L, ds->K, n_sub, errors_out, s, ctx.d_status));
     return DEOCT_OK;
   } catch (...) {
     return set_error(DEOCT_ERR_INVALID, "internal exception");

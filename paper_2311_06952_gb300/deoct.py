@@ -34,7 +34,7 @@ EXPORTED = [
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
     "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
     "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
-    "deoct_selftest_wait",
+    "deoct_selftest_wait", "deoct_encode_auto",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -93,6 +93,7 @@ def load(path: str | None = None):
             "deoct_selftest_wait": [_vp, _i32, _vp],
             "deoct_encode": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp],
             "deoct_encode_ex": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
+            "deoct_encode_auto": [_vp, _vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp],
             "deoct_split_values": [_vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp],
             "deoct_predict": [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
             "deoct_decode_population": [_vp, ctypes.POINTER(Dataset), _vp, _i32, _i32, _vp, _vp, _vp],
@@ -142,6 +143,23 @@ def _ptr(t, itemsize=None):
     if itemsize is not None and t.element_size() != itemsize:
         raise ValueError("tensor element size %d, expected %d" % (t.element_size(), itemsize))
     return _vp(t.data_ptr())
+
+
+_EMPTY_IDX = {}
+
+
+def _idx_ptr(sample_idx):
+    """Address of a sample index tensor.  An empty index (the empty subset) still needs a
+    non-NULL pointer -- NULL means "all samples" in the C ABI -- but torch reports address 0
+    for tensors without elements, so a one-element placeholder on the same device stands in
+    (never read: the library reads no index when n_sub = 0)."""
+    if sample_idx is None or sample_idx.numel() > 0:
+        return _ptr(sample_idx, 4)
+    import torch
+    dev = sample_idx.device
+    if dev not in _EMPTY_IDX:
+        _EMPTY_IDX[dev] = torch.zeros(4, dtype=torch.int32, device=dev)
+    return _ptr(_EMPTY_IDX[dev], 4)
 
 
 def _stream(stream):
@@ -249,6 +267,26 @@ def deoct_encode_ex(ctx: Context, X, rank_bytes: int, stream=None):
     return ranks, nu, uniq
 
 
+def deoct_encode_auto(ctx: Context, X, want_unique=True, stream=None):
+    """a1 with the rank width chosen from n_p (uint16 when every n_p <= 65536):
+    (ranks [F][ld], n_unique [F], unique [F][ld] float32 or None, rank_bytes); sync."""
+    import torch
+    n, F = X.shape
+    ld = (n + 7) // 8 * 8
+    buf = torch.empty(F * ld, dtype=torch.int32, device=X.device)
+    nu = torch.empty(F, dtype=torch.int32, device=X.device)
+    uniq = torch.empty((F, ld), dtype=torch.float32, device=X.device) if want_unique else None
+    w = ctypes.c_int32()
+    _check(load().deoct_encode_auto(ctx.handle, _ptr(X, 4), n, F, _ptr(buf), ld, _ptr(nu, 4),
+                                    _ptr(uniq), ctypes.byref(w), _stream(stream)))
+    if w.value == 2:
+        # the rows were written as uint16 [F][ld] into the first half: keep only those bytes
+        ranks = buf.view(torch.int16)[: F * ld].view(F, ld).clone()
+    else:
+        ranks = buf.view(F, ld)
+    return ranks, nu, uniq, w.value
+
+
 def deoct_split_values(ctx: Context, unique, a, theta, stream=None):
     """Raw-unit thresholds b [B] (float64, device) of a fitted tree (a, theta: device [B])."""
     import torch
@@ -271,7 +309,11 @@ def deoct_predict(ctx: Context, X, a, b, depth: int, leaf_class, y=None, stream=
 
 
 def encode_dataset(ctx: Context, X, y, K: int, rank_bytes: int, stream=None) -> DeviceDataset:
-    ranks, nu = deoct_encode(ctx, X, rank_bytes, stream=stream)
+    """Encode X and bundle it with the labels; rank_bytes 0 picks the width from n_p."""
+    if rank_bytes == 0:
+        ranks, nu, _, rank_bytes = deoct_encode_auto(ctx, X, want_unique=False, stream=stream)
+    else:
+        ranks, nu = deoct_encode(ctx, X, rank_bytes, stream=stream)
     return DeviceDataset(ranks, rank_bytes, nu, y, X.shape[0], X.shape[1], K)
 
 
@@ -299,7 +341,7 @@ def deoct_eval_population(ctx: Context, ds: DeviceDataset, a, theta, depth: int,
     if errors_out is None:
         errors_out = torch.empty(P, dtype=torch.int32, device=a.device)
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_eval_population(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+    _check(load().deoct_eval_population(ctx.handle, ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub,
                                         _ptr(a, 2), _ptr(theta, 4), P, depth, _ptr(counts_out, 4),
                                         _ptr(errors_out, 4), _stream(stream)))
     return counts_out, errors_out
@@ -323,7 +365,7 @@ def deoct_de_init(ctx: Context, ds: DeviceDataset, params: Params, stream_id=0, 
         best = torch.empty(1, dtype=torch.int32, device=dev)
     S = 0 if seeds is None else seeds.shape[0]
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_de_init(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+    _check(load().deoct_de_init(ctx.handle, ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub,
                                 ctypes.byref(params), stream_id, _ptr(seeds, 4), S, _ptr(pop, 4),
                                 _ptr(fitness, 8), _ptr(best, 4), _stream(stream)))
     return pop, fitness, best
@@ -332,7 +374,7 @@ def deoct_de_init(ctx: Context, ds: DeviceDataset, params: Params, stream_id=0, 
 def deoct_de_step(ctx: Context, ds: DeviceDataset, params: Params, generation: int, pop, fitness,
                   best, stream_id=0, sample_idx=None, stream=None):
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_de_step(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx, 4), n_sub,
+    _check(load().deoct_de_step(ctx.handle, ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub,
                                 ctypes.byref(params), stream_id, generation, _ptr(pop, 4), _ptr(fitness, 8),
                                 _ptr(best, 4), _stream(stream)))
     return pop, fitness, best
@@ -347,7 +389,7 @@ def deoct_fit_subtree(ctx: Context, ds: DeviceDataset, params: Params, stream_id
     fit = ctypes.c_double()
     S = 0 if seeds is None else seeds.shape[0]
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_fit_subtree(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx), n_sub,
+    _check(load().deoct_fit_subtree(ctx.handle, ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub,
                                     ctypes.byref(params), stream_id, _ptr(seeds), S, _ptr(a), _ptr(th),
                                     ctypes.byref(fit), _ptr(pop_out), _stream(stream)))
     return a, th, fit.value
@@ -374,7 +416,7 @@ def deoct_depth1_search(ctx: Context, ds: DeviceDataset, sample_idx=None, n_min=
     th = ctypes.c_uint32()
     f = ctypes.c_double()
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_depth1_search(ctx.handle, ctypes.byref(ds.c), _ptr(sample_idx), n_sub, n_min,
+    _check(load().deoct_depth1_search(ctx.handle, ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub, n_min,
                                       alpha, ctypes.byref(a), ctypes.byref(th), ctypes.byref(f),
                                       _stream(stream)))
     return a.value, th.value, f.value
@@ -388,7 +430,7 @@ def deoct_eval_population_noalloc(ds: DeviceDataset, a, theta, depth: int, count
     device; calls whose GPU work overlaps must be serialised by the caller."""
     P = a.shape[0]
     n_sub = ds.n if sample_idx is None else sample_idx.numel()
-    _check(load().deoct_eval_population_noalloc(ctypes.byref(ds.c), _ptr(sample_idx), n_sub, _ptr(a),
+    _check(load().deoct_eval_population_noalloc(ctypes.byref(ds.c), _idx_ptr(sample_idx), n_sub, _ptr(a),
                                                 _ptr(theta), P, depth, _ptr(counts_out), _ptr(errors_out),
                                                 _stream(stream)))
     return counts_out, errors_out

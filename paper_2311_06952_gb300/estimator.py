@@ -62,8 +62,8 @@ class MHDEOCTClassifier:
         yd = self._dev(y, torch.uint8)
         n, F = Xd.shape
         K = int(K) if K is not None else int(yd.max().item()) + 1
-        rank_bytes = 2 if n <= 65536 else 4
-        ranks, nu, uniq = deoct.deoct_encode_ex(ctx, Xd, rank_bytes)
+        # uint16 ranks whenever every feature has at most 65536 distinct values
+        ranks, nu, uniq, rank_bytes = deoct.deoct_encode_auto(ctx, Xd)
         ds = deoct.DeviceDataset(ranks, rank_bytes, nu, yd, n, F, K)
         flags = (deoct.DEOCT_BATCHED if self.batched else 0) | \
             (deoct.DEOCT_DITHER_M if self.params["dither"] else 0) | \

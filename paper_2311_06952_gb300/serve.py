@@ -196,11 +196,9 @@ def fit_on_stream(ctx, req: FitRequest, stream):
     import torch
 
     from . import deoct
-    n, F = req.X.shape
-    W = rank_width(n)
     Xd = torch.from_numpy(np.ascontiguousarray(req.X, np.float32)).to("cuda", non_blocking=False)
     yd = torch.from_numpy(np.ascontiguousarray(req.y, np.uint8)).to("cuda", non_blocking=False)
-    ds = deoct.encode_dataset(ctx, Xd, yd, req.K, W, stream=stream)
+    ds = deoct.encode_dataset(ctx, Xd, yd, req.K, 0, stream=stream)  # width from n_p
     prm = deoct.make_params(req.depth, req.pop, req.gens, mut_f=req.mut_f, cr=req.cr, alpha=req.alpha,
                             n_min=req.n_min, seed=req.seed, horizon=req.horizon,
                             flags=deoct.DEOCT_BATCHED if req.batched else 0)

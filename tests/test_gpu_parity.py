@@ -83,6 +83,33 @@ def test_encode_rejects_nan_and_narrow_width(c):
     assert u32(ds.n_unique)[0] == 10
 
 
+@pytest.mark.parametrize("name,want_w", [("w3_small", 2), ("continuous_u32", 4), ("one_sample", 2),
+                                         ("exactly_65536", 2), ("exactly_65537", 4)])
+def test_encode_auto_width_from_n_p(c, name, want_w):
+    """The automatic width is uint16 exactly when every n_p <= 65536, whatever n is; the ranks
+    and the distinct values equal the oracle's."""
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    if name.startswith("exactly_"):
+        m = int(name.split("_")[1])
+        rng = _rng(m)
+        X = np.stack([rng.permutation(np.arange(m, dtype=np.float32) / 7),
+                      rng.integers(0, 5, m).astype(np.float32)], axis=1)
+        X = np.concatenate([X, X[: 1000]])  # n > n_p
+    else:
+        X, _ = _encode_case(name)
+    ranks, nu, uniq, w = deoct.deoct_encode_auto(c, to_dev(np.ascontiguousarray(X, np.float32)))
+    assert w == want_w
+    assert ranks.element_size() == w and ranks.shape[1] % 8 == 0
+    r_ref, nu_ref = oracle.encode(X)
+    np.testing.assert_array_equal(u32(nu), nu_ref)
+    got = (u16(ranks) if w == 2 else u32(ranks))[:, : len(X)].astype(np.uint32)
+    np.testing.assert_array_equal(got, r_ref)
+    u = uniq.cpu().numpy()
+    for p in range(X.shape[1]):
+        np.testing.assert_array_equal(u[p, : nu_ref[p]], np.unique(np.where(X[:, p] == 0, 0, X[:, p])))
+
+
 # --------------------------------------------------------------------------
 # a3 + a4: evaluator
 # --------------------------------------------------------------------------
