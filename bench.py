@@ -274,7 +274,10 @@ def mh_compare(args):
     ds = deoct.encode_dataset(ctx, torch.from_numpy(w["X"]).cuda(), torch.from_numpy(w["y"]).cuda(),
                               w["K"], 4)
     res = {}
-    for name, flags in (("batched", deoct.DEOCT_BATCHED), ("plain", 0)):
+    forms = (("batched", deoct.DEOCT_BATCHED), ("plain", 0))
+    if args.mh_form != "both":
+        forms = tuple(f for f in forms if f[0] == args.mh_form)
+    for name, flags in forms:
         prm = deoct.make_params(w["depth"], w["P"], w["G"], mut_f=w["M"], cr=w["CR"], seed=w["seed"],
                                 horizon=w["horizon"], flags=flags)
         if name == "batched":
@@ -285,6 +288,11 @@ def mh_compare(args):
         out = deoct.deoct_fit_moving_horizon(ctx, ds, prm)
         torch.cuda.synchronize()
         res[name] = (time.perf_counter() - t0, out, ctx.stats()["launches"])
+    if args.mh_form != "both":
+        t, o, l = res[args.mh_form]
+        ctx.close()
+        return {"workload": MH_WORKLOAD, "form": args.mh_form, "seconds": t, "launches": int(l),
+                "subtree_solves": int(np.sum(o["kind"] > 0)), "solves_per_s": float(np.sum(o["kind"] > 0)) / t}
     tb, ob, lb = res["batched"]
     tp, op, lp = res["plain"]
     same = all(np.array_equal(ob[k], op[k]) for k in ("a", "theta", "kind", "node_fit", "leaf_class"))
@@ -302,48 +310,65 @@ def mh_compare(args):
             "batched_launches": int(lb), "plain_launches": int(lp)}
 
 
-def run_serve(args):
-    """Serving workload: Poisson arrivals at 20 req/s, mixed n, F, K, depth, horizon.
-    Continuous batching (slots + 120 GB budget, overlapping streams) against the same
-    requests solved one at a time with the plain per-node form, FIFO, same arrivals."""
+SERVE_WORKLOAD = ("serving: Poisson arrivals at 20 req/s, n log-uniform [1e3, 2e6], F U{4..60}, K U{2..10}, "
+                  "depth U{2..6}, horizon U{2,3}, Gaussian-mixture features, planted-tree labels 5% flips, "
+                  "P=128, G=200, M=0.5, CR=0.9, 120 GB budget")
+
+
+def _serve_trace(raw, slots, engine):
+    """Serve the trace (arrival times as generated) and return the results and the server's figures."""
     import torch
-    from paper_2311_06952_gb300 import build as _build
-    from paper_2311_06952_gb300 import datagen, deoct, serve
-    _build.build()
-    raw = datagen.serving_requests(num=args.serve, rate=20.0, materialize=True)  # not timed
-    mk = lambda r, batched: serve.FitRequest(X=r["X"], y=r["y"], K=r["K"], depth=r["depth"],
-                                             horizon=r["horizon"], pop=128, gens=200, seed=r["id"],
-                                             id=r["id"], arrival=r["arrival"], batched=batched)
-    # warm-up (not timed): one request per slot so every slot has its context and kernels ready
-    srv = serve.Server(budget_bytes=120 << 30, slots=args.slots)
-    warm = [mk(r, True) for r in raw[: args.slots]]
-    for i, w in enumerate(warm):
-        w.arrival = 0.0
+    from paper_2311_06952_gb300 import serve
+    mk = lambda r: serve.FitRequest(X=r["X"], y=r["y"], K=r["K"], depth=r["depth"], horizon=r["horizon"],
+                                    pop=128, gens=200, seed=r["id"], id=r["id"], arrival=r["arrival"])
+    srv = serve.Server(budget_bytes=120 << 30, slots=slots, engine=engine)
     try:
+        warm = [mk(r) for r in raw[:slots]]  # not timed: every slot gets its context and kernels ready
+        for w in warm:
+            w.arrival = 0.0
         serve.run_trace(srv, warm)
-    except Exception:
-        srv.close()
-        raise
-    srv.peak_in_use = 0
-    srv.max_concurrent = 0
-    reqs = [mk(r, True) for r in raw]
-    t0 = srv.now()
-    try:
-        res = serve.run_trace(srv, reqs)
+        st0 = srv.engine_stats()
+        srv.max_concurrent = 0
+        srv.peak_charged = srv.charged
+        torch.cuda.reset_peak_memory_stats()
+        t0 = srv.now()
+        res = serve.run_trace(srv, [mk(r) for r in raw])
         t1 = srv.now()
+        st1 = srv.engine_stats()
+        held = sum(srv.retained) + torch.cuda.max_memory_reserved()
     finally:
         srv.close()
-    lat = serve.latency_stats([r.latency for r in res])
-    served = {"requests": len(res), "makespan_s": t1 - t0, "throughput_rps": len(res) / (t1 - t0),
-              "latency": lat, "slots": args.slots, "budget_bytes": 120 << 30,
-              "peak_budget_in_use": srv.peak_in_use, "max_concurrent": srv.max_concurrent}
-    # sequential plain baseline
+    out = {"requests": len(res), "makespan_s": t1 - t0, "throughput_rps": len(res) / (t1 - t0),
+           "latency": serve.latency_stats([r.latency for r in res]), "slots": slots,
+           "budget_bytes": 120 << 30, "peak_charged_bytes": srv.peak_charged,
+           "device_bytes_held": int(held), "max_concurrent": srv.max_concurrent,
+           "scratch_growth_within_reserve": bool(all(r.scratch_after - r.scratch_before <= r.scratch_reserve
+                                                     for r in res))}
+    if st1 is not None:
+        out["engine"] = {k: st1[k] - st0[k] if k not in ("max_jobs_per_launch", "max_problems_per_launch")
+                         else st1[k] for k in st1}
+    return res, out
+
+
+def serve_compare(num, slots):
+    """The serving workload's first `num` requests: served with the shared engine (launches
+    carrying several requests' generations), served with a stream per request, and solved
+    one at a time with the plain per-node form (FIFO, same arrivals)."""
+    import torch
+    from paper_2311_06952_gb300 import datagen, deoct, serve
+    raw = datagen.serving_requests(num=num, rate=20.0, materialize=True)  # not timed
+    res_e, eng = _serve_trace(raw, slots, True)
+    res_s, strm = _serve_trace(raw, slots, False)
+    by_e = {r.id: r for r in res_e}
+    by_s = {r.id: r for r in res_s}
+    keys = ("a", "theta", "kind", "node_fit", "leaf_class")
+    same = all(np.array_equal(getattr(by_e[i], k), getattr(by_s[i], k)) for i in by_e for k in keys)
     ctx = deoct.Context(0)
     stream = torch.cuda.Stream()
-    service, same = [], True
-    by_id = {r.id: r for r in res}
+    service = []
     for r in raw:
-        q = mk(r, False)
+        q = serve.FitRequest(X=r["X"], y=r["y"], K=r["K"], depth=r["depth"], horizon=r["horizon"], pop=128,
+                             gens=200, seed=r["id"], id=r["id"], arrival=r["arrival"], batched=False)
         with torch.cuda.stream(stream):
             if r is raw[0]:
                 serve.fit_on_stream(ctx, q, stream)  # warm-up
@@ -352,20 +377,26 @@ def run_serve(args):
             out = serve.fit_on_stream(ctx, q, stream)
             torch.cuda.synchronize()
             service.append(time.perf_counter() - ts)
-        ref = by_id[r["id"]]
-        same = same and all(np.array_equal(getattr(ref, k), out[k])
-                            for k in ("a", "theta", "kind", "node_fit", "leaf_class"))
+        same = same and all(np.array_equal(getattr(by_e[r["id"]], k), out[k]) for k in keys)
     ctx.close()
     seq_lat = serve.sequential_queue_latencies([r["arrival"] for r in raw], service)
     seq_makespan = max(a + l for a, l in zip([r["arrival"] for r in raw], seq_lat))
-    line = {"mode": "serving", "metric": "p50/p99 request latency and requests/s",
-            "workload": "serving: %d requests, Poisson 20/s, n log-uniform [1e3, 2e6], F U{4..60}, "
-                        "K U{2..10}, depth U{2..6}, horizon U{2,3}, P=128, G=200" % len(raw),
-            "served": served,
+    return {"metric": "p50/p99 request latency and requests/s", "workload": SERVE_WORKLOAD,
+            "requests": num, "served_engine": eng, "served_streams": strm,
             "sequential_plain": {"latency": serve.latency_stats(seq_lat),
-                                 "throughput_rps": len(raw) / seq_makespan,
+                                 "throughput_rps": num / seq_makespan,
                                  "service_s_total": float(np.sum(service))},
-            "identical_trees_served_vs_alone_plain": bool(same), "data": "synthetic"}
+            "engine_vs_streams": {"p99": eng["latency"]["p99_s"] / strm["latency"]["p99_s"],
+                                  "p50": eng["latency"]["p50_s"] / strm["latency"]["p50_s"],
+                                  "throughput": eng["throughput_rps"] / strm["throughput_rps"]},
+            "identical_trees_engine_streams_plain": bool(same), "data": "synthetic"}
+
+
+def run_serve(args):
+    """Serving workload with --serve requests (all 500: the full trace)."""
+    from paper_2311_06952_gb300 import build as _build
+    _build.build()
+    line = dict(mode="serving", **serve_compare(args.serve, args.slots))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -737,6 +768,10 @@ def run_ours(args):
         line["p_sweep"] = eval_p_sweep(ctx, ranks, nu, yd, n, F, K, peaks)
         line["population_eval"] = eval_workload1(args)
         line["mh_batched_vs_plain"] = mh_compare(args)
+    if world == 1 and args.serve_default > 0:
+        del Xd, ranks
+        torch.cuda.empty_cache()
+        line["serving"] = serve_compare(args.serve_default, args.slots)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(dict(w, X=data["X"], y=data["y"]))
     print(json.dumps(line), flush=True)
@@ -762,8 +797,12 @@ def main():
     ap.add_argument("--mh-n", type=int, default=1_000_000)
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many requests")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-default", type=int, default=60,
+                    help="requests of the serving trace in the default line (0: none)")
     ap.add_argument("--table3", default="", help="comma list of bitcoin-heist,susy,higgs")
     ap.add_argument("--mh-only", action="store_true", help="only the batched-vs-plain moving-horizon line")
+    ap.add_argument("--mh-form", choices=["both", "batched", "plain"], default="both",
+                    help="with --mh-only: time one form alone (a batched run is preceded by a warm-up fit)")
     ap.add_argument("--p-eval", type=int, default=0, help="only single evaluations of this many trees")
     ap.add_argument("--stream-scan", action="store_true",
                     help="only single evaluations of 1 and 2 trees for n = 1e6..1e7 beside a torch reduction")

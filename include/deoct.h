@@ -302,6 +302,64 @@ DEOCT_API int deoct_predict(deoct_ctx* ctx, const float* X, int64_t m, int32_t F
                             const uint8_t* y, uint8_t* pred_out, uint64_t* correct_out,
                             void* stream);
 
+/* ---- a8: serving, continuous batching across jobs -------------------------
+ * The paper solves one training problem at a time; a service fits many trees
+ * at once.  An engine runs the DEOCT generations of the batched level solves
+ * (Algorithm 2 with DEOCT_BATCHED, Algorithm 4) of every context attached to
+ * it in shared launches: per tick, one evaluator launch and one DE-step launch
+ * cover the problems of all resident jobs that share the rank width, the
+ * subtree depth and the DE constants (population, M, CR, alpha, n_min,
+ * dither).  A job's host thread still runs its own per-level work (histogram,
+ * compaction, depth-1 search, initial population) on its own stream, then
+ * hands the level's problems to the engine and waits; problems join at any
+ * tick and leave after their own G generations.  Every problem keeps its
+ * Philox key (seed, node id) and its own generation counter, so a job's tree
+ * is identical alone and in any mix.
+ *  deoct_engine_create   starts the engine (its own stream and host thread)
+ *                        on `device`; deoct_engine_destroy stops it once the
+ *                        submitted work is done (call it after every attached
+ *                        context has finished its calls).
+ *  deoct_engine_attach   routes the batched level solves of `ctx` through `e`
+ *                        (NULL detaches).  Contexts stay single-threaded; the
+ *                        engine may serve any number of them from as many host
+ *                        threads.  Device errors in a shared launch are
+ *                        returned to the jobs whose problems finish with it.
+ *  deoct_engine_get_stats counters since creation. */
+/* deoct_get_memory: the device bytes `ctx` holds (its scratch, grow-only until
+ * deoct_destroy, plus its status word) and its pinned host staging bytes.
+ * deoct_fit_scratch_bound: an upper bound of the device bytes by which `ctx`'s
+ * scratch grows when it encodes an n x F set (rank_bytes 2 or 4, or 0 for the
+ * widest choice of deoct_encode_auto) and fits it with
+ * deoct_fit_moving_horizon under `params` (plain or batched, with or without
+ * warm starts); with ctx NULL, the bytes a fresh context holds afterwards.  The
+ * scratch is kept per buffer, so a context holding more bytes in total than a
+ * request needs may still grow.  The caller's own arrays (features, ranks,
+ * labels) are not included.  Neither call touches the GPU; ctx must not be in
+ * use by another thread. */
+DEOCT_API int deoct_get_memory(deoct_ctx* ctx, uint64_t* device_bytes, uint64_t* pinned_bytes);
+/* deoct_release_scratch: frees every scratch buffer of `ctx` (the next calls
+ * allocate again).  Synchronises the device.  sync. */
+DEOCT_API int deoct_release_scratch(deoct_ctx* ctx);
+DEOCT_API int deoct_fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int32_t F, int32_t K,
+                                      int32_t rank_bytes, const deoct_params* params,
+                                      uint64_t* bytes_out);
+
+typedef struct deoct_engine deoct_engine;
+typedef struct {
+  uint64_t submissions;        /* level solves handed to the engine */
+  uint64_t completed;          /* level solves returned */
+  uint64_t ticks;              /* generations run (replays of the shared launches) */
+  uint64_t launches;           /* kernel launches in those replays */
+  uint64_t eval_launches;      /* of which evaluator launches */
+  uint64_t shared_launches;    /* launches carrying problems of two or more jobs */
+  uint64_t max_jobs_per_launch;
+  uint64_t max_problems_per_launch;
+} deoct_engine_stats;
+DEOCT_API int deoct_engine_create(deoct_engine** out, int device);
+DEOCT_API int deoct_engine_destroy(deoct_engine* e);
+DEOCT_API int deoct_engine_attach(deoct_ctx* ctx, deoct_engine* e);
+DEOCT_API int deoct_engine_get_stats(deoct_engine* e, deoct_engine_stats* out);
+
 /* ---- evaluation without device allocation --------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory -- a host framework that owns all device memory

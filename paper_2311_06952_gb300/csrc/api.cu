@@ -400,6 +400,45 @@ int deoct_reset_stats(deoct_ctx* ctx) {
   API_END
 }
 
+int deoct_get_memory(deoct_ctx* ctx, uint64_t* device_bytes, uint64_t* pinned_bytes) {
+  API_BEGIN
+  if (!ctx) return set_error(DEOCT_ERR_INVALID, "context is NULL");
+  uint64_t d = ctx->d_status ? sizeof(int) : 0;
+  for (int i = 0; i < SL_COUNT; ++i) d += ctx->scratch[i].bytes;
+  if (device_bytes) *device_bytes = d;
+  if (pinned_bytes) *pinned_bytes = ctx->h_pinned_bytes;
+  return DEOCT_OK;
+  API_END
+}
+
+int deoct_release_scratch(deoct_ctx* ctx) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  for (int i = 0; i < SL_COUNT; ++i)
+    if (ctx->scratch[i].ptr) {
+      DEOCT_CUDA_TRY(cudaFree(ctx->scratch[i].ptr));  // synchronises the device
+      ctx->scratch[i].ptr = nullptr;
+      ctx->scratch[i].bytes = 0;
+    }
+  return DEOCT_OK;
+  API_END
+}
+
+int deoct_fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int32_t F, int32_t K, int32_t rank_bytes,
+                            const deoct_params* params, uint64_t* bytes_out) {
+  API_BEGIN
+  if (!params || !bytes_out) return set_error(DEOCT_ERR_INVALID, "NULL argument");
+  if (n < 1 || n > kMaxN || F < 1 || F > kMaxF || K < 1 || K > kMaxK)
+    return set_error(DEOCT_ERR_INVALID, "bad n, F or K");
+  if (rank_bytes != 0 && rank_bytes != 2 && rank_bytes != 4)
+    return set_error(DEOCT_ERR_INVALID, "rank_bytes must be 0, 2 or 4");
+  if (params->depth < 1 || params->depth > kMaxDepth) return set_error(DEOCT_ERR_INVALID, "bad depth");
+  *bytes_out = (uint64_t)fit_scratch_bound(ctx, n, F, K, rank_bytes == 2 ? 2 : 4, params) +
+               (ctx ? 0 : sizeof(int));
+  return DEOCT_OK;
+  API_END
+}
+
 int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, int32_t grid) {
   API_BEGIN
   CTX_CHECK(ctx);

@@ -103,6 +103,9 @@ struct deoct_ctx {
   std::vector<std::pair<uint64_t, std::array<int, 3>>> tuned;
   // evaluator launch shape forced by deoct_set_eval_config (0 = automatic)
   int force_S = 0, force_TG = 0, force_warps = 0, force_grid = 0;
+  // shared engine that runs the generations of this context's batched level
+  // solves together with other contexts' (deoct_engine_attach; nullable)
+  deoct_engine* engine = nullptr;
 };
 
 namespace deoct {

@@ -165,6 +165,13 @@ int radix_sort_segments(deoct_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1
 // ---------------------------------------------------------------------------
 // moving horizon (mh.cu)
 // ---------------------------------------------------------------------------
+// engine.cu: run G generations of problems in steady state (trials of generation
+// 1 built, counts zeroed) in the shared launches of engine `e`; returns when the
+// last has completed.  W, Dt: rank width and subtree depth of the problems.
+int engine_generations(deoct_engine* e, const void* owner, int W, int Dt, const DEArgs& a, int G,
+                       const std::vector<DEProb>& dp, const std::vector<EvalProb>& ep);
+
+size_t fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int F, int K, int W, const deoct_params* prm);
 int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uint16_t* a_out,
            uint32_t* th_out, uint8_t* leaf_class_out, int32_t* kind_out, double* node_fit_out,
            cudaStream_t s);

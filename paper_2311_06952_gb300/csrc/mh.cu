@@ -476,6 +476,29 @@ int build_plan(deoct_ctx* ctx, BatchedEval* be, const EvalConfig& cfg, int F, in
   return DEOCT_OK;
 }
 
+// root node (a, theta) and fitness of each problem's best individual -> host
+int extract_roots(deoct_ctx* ctx, const DEProb* ddp, int M, int B, std::vector<uint16_t>* ra,
+                  std::vector<uint32_t>* rth, std::vector<double>* rf, cudaStream_t s) {
+  unsigned char* dres;
+  DEOCT_TRY(scratch_get(ctx, SL_D1_RESULT, (size_t)M * 16 + 64, (void**)&dres));
+  double* df = reinterpret_cast<double*>(dres);
+  uint32_t* dth = reinterpret_cast<uint32_t*>(dres + (size_t)M * 8);
+  uint16_t* da = reinterpret_cast<uint16_t*>(dres + (size_t)M * 12);
+  extract_roots_kernel<<<(M + 127) / 128, 128, 0, s>>>(ddp, M, B, da, dth, df);
+  count_launch(ctx);
+  DEOCT_TRY(check_launch("extract_roots_kernel"));
+  DEOCT_TRY(download(ctx, df, M, rf, s));
+  DEOCT_TRY(download(ctx, dth, M, rth, s));
+  DEOCT_TRY(download(ctx, da, M, ra, s));
+  return DEOCT_OK;
+}
+
+int64_t nsum_of(const Compacted& c, int M) {
+  int64_t t = 0;
+  for (int m = 0; m < M; ++m) t += c.counts[m];
+  return t;
+}
+
 uint64_t tune_key(int W, int D, int F, int K, int P, int64_t npad, int M) {
   auto lg = [](int64_t x) {
     int r = 0;
@@ -564,6 +587,18 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   a.dither = (prm->flags & DEOCT_DITHER_M) ? 1 : 0;
   a.status = ctx->d_status;
   DEOCT_TRY(de_launch_init(ctx, a, s));
+
+  if (ctx->engine) {
+    // S^1 and the first trials here, then the G generations in the engine's
+    // launches shared with other jobs
+    EvalConfig cfg = eval_choose_config(ctx, W, Dt, F, K, P, std::max<int64_t>(1, nsum_of(c, M)), M);
+    DEOCT_TRY(build_plan(ctx, &be, cfg, F, K, P, s));
+    DEOCT_TRY(eval_launch(ctx, W, Dt, be.plan, cfg, s));
+    DEOCT_TRY(de_launch_step(ctx, a, 0, DE_FIRST | DE_GEN_DEVICE | (prm->gens >= 1 ? DE_TRIAL : 0), s));
+    DEOCT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (prm->gens >= 1) DEOCT_TRY(engine_generations(ctx->engine, ctx, W, Dt, a, prm->gens, dp, be.probs));
+    return extract_roots(ctx, ddp, M, B, ra, rth, rf, s);
+  }
 
   // ---- evaluator shape: autotuned once per workload class -------------------
   int64_t nsum = 0;
@@ -671,18 +706,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     if (ce != cudaSuccess) return set_error(DEOCT_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(ce));
     if (ce2 != cudaSuccess) return set_error(DEOCT_ERR_CUDA, "generation loop failed: %s", cudaGetErrorString(ce2));
   }
-  unsigned char* dres;
-  DEOCT_TRY(scratch_get(ctx, SL_D1_RESULT, (size_t)M * 16 + 64, (void**)&dres));
-  double* df = reinterpret_cast<double*>(dres);
-  uint32_t* dth = reinterpret_cast<uint32_t*>(dres + (size_t)M * 8);
-  uint16_t* da = reinterpret_cast<uint16_t*>(dres + (size_t)M * 12);
-  extract_roots_kernel<<<(M + 127) / 128, 128, 0, s>>>(ddp, M, B, da, dth, df);
-  count_launch(ctx);
-  DEOCT_TRY(check_launch("extract_roots_kernel"));
-  DEOCT_TRY(download(ctx, df, M, rf, s));
-  DEOCT_TRY(download(ctx, dth, M, rth, s));
-  DEOCT_TRY(download(ctx, da, M, ra, s));
-  return DEOCT_OK;
+  return extract_roots(ctx, ddp, M, B, ra, rth, rf, s);
 }
 
 // Plain form: one DEOCT (own launches) per node segment.
@@ -1116,6 +1140,74 @@ int mh_run(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* prm, uin
   if (kind_out) memcpy(kind_out, kind.data(), sizeof(int32_t) * B);
   if (node_fit_out) memcpy(node_fit_out, nf.data(), sizeof(double) * B);
   return DEOCT_OK;
+}
+
+// The largest request of every scratch slot on the path of deoct_encode_auto
+// (or deoct_encode of width W) followed by deoct_fit_moving_horizon on an n x F
+// set; mirrors the allocation sites above and in encode.cu.  A context that
+// holds have[s] bytes in slot s grows it to need + need / 8 (scratch_get's
+// headroom) when need > have[s]; with ctx == nullptr every slot starts empty.
+size_t fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int F, int K, int W, const deoct_params* prm) {
+  std::vector<size_t> slot(SL_COUNT, 0);
+  auto need = [&](int sl, double bytes) { slot[sl] = std::max(slot[sl], (size_t)bytes); };
+  const int D = prm->depth, H = std::max(1, prm->horizon), P = std::max(prm->pop, 1);
+  const int Lf = 1 << D, nn = Lf / 2;  // at most 2^(D-1) nodes on a level
+  const double nF = (double)n * F;
+  const int64_t tiles = (n + 2047) / 2048;
+  // encoder
+  for (int sl : {SL_ENC_K0, SL_ENC_K1, SL_ENC_V0, SL_ENC_V1}) need(sl, 4.0 * nF);
+  need(SL_ENC_TILE, 4.0 * F * tiles);
+  need(SL_ENC_HIST, 4.0 * F * 256 * tiles);
+  need(SL_ENC_TOT, 4.0 * F * 256);
+  // moving horizon: level state and compacted segments
+  const int64_t npad = round_up(n + (int64_t)kSegAlign * nn, 64);
+  const int64_t ptiles = (npad + 2047) / 2048;
+  need(SL_MH_NODEOF, 4.0 * n);
+  need(SL_MH_HOSTBUF, 4.0 * 2 * Lf * K + 64);
+  need(SL_MH_IDX, 4.0 * npad);
+  need(SL_MISC, std::max(4.0 * npad, 8.0 + 6.0 * (Lf - 1) + 80));
+  need(SL_MH_RANKS, (double)F * npad * W);
+  need(SL_MH_LABELS, (double)npad);
+  for (int sl : {SL_MH_D1KEYS, SL_MH_D1VALS, SL_MH_D1K1, SL_MH_D1V1}) need(sl, 4.0 * F * npad);
+  need(SL_ENC_HIST, 4.0 * F * 256 * ptiles);
+  // DEOCT subproblems of a level (subtree depth <= min(horizon, D)); the greedy
+  // warm starts work on (node, subtree node) pairs: at most nn * L / 2 of them
+  const int Dt = std::min(H, D), B = (1 << Dt) - 1, L = 1 << Dt;
+  const double pairs = (double)nn * std::max(1, L / 2);
+  need(SL_MH_STATS, std::max(8.0 * pairs, 4.0 * pairs * K));
+  need(SL_MH_SEG, std::max(4.0 * pairs, 8.0 * 255));
+  need(SL_MH_CURSOR, std::max(4.0 * pairs, 8.0 * 255));
+  need(SL_MH_D1BEST, 12.0 * 255 * F + 64);
+  need(SL_D1_RESULT, std::max(16.0 * std::max<double>(pairs, 255) + 64, 6.0 * (Lf - 1) + 64));
+  const double per = (double)P * 2 * B * 4 * 2 + (double)P * 8 * 2 + 16 + (double)P * B * 4 +
+                     (double)P * L * K * 4 + 6 * 15 + 256;
+  need(SL_MH_POP, per * nn);
+  need(SL_DE_PROBS, (double)sizeof(DEProb) * nn);
+  need(SL_EVAL_PROBS, (double)sizeof(EvalProb) * nn);
+  need(SL_EVAL_JOBS, (double)sizeof(EvalJob) * nn * (P + 1) * std::max<int64_t>(1, 1 + n / 128 / nn));
+  // plain form and warm starts: one DEOCT's buffers, the seeds, the greedy subtrees
+  const int Bf = Lf - 1;
+  need(SL_POP, 4.0 * P * 2 * Bf);
+  need(SL_FIT, 8.0 * P);
+  need(SL_BEST, 64);
+  need(SL_POP_TRIAL, 4.0 * P * 2 * Bf);
+  need(SL_FIT_TRIAL, 8.0 * P);
+  need(SL_NODES, 4.0 * P * Bf);
+  need(SL_COUNTS, 4.0 * P * Lf * K);
+  need(SL_GEN, 4);
+  need(SL_MH_SEEDS, 4.0 * 2 * nn * 2 * B);
+  need(SL_MH_SUB, 4.0 * npad);
+  need(SL_MH_SUBHIST, 4.0 * pairs * K);
+  need(SL_MH_IDX2, 4.0 * npad);
+  need(SL_MH_POS2, 4.0 * npad);
+  need(SL_MH_RANKS2, (double)F * npad * W);
+  need(SL_MH_LABELS2, (double)npad);
+  size_t total = 0;
+  for (int i = 0; i < SL_COUNT; ++i) {
+    const size_t have = ctx ? ctx->scratch[i].bytes : 0;
+    if (slot[i] > have) total += slot[i] + slot[i] / 8 - have;
+  }
+  return total;
 }
 
 // exhaustive depth-1 search on one sample subset

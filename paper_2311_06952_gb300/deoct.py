@@ -34,7 +34,9 @@ EXPORTED = [
     "deoct_decode_population", "deoct_eval_population", "deoct_de_init", "deoct_de_step",
     "deoct_fit_subtree", "deoct_fit_moving_horizon", "deoct_depth1_search", "deoct_set_eval_config",
     "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
-    "deoct_selftest_wait", "deoct_encode_auto",
+    "deoct_selftest_wait", "deoct_encode_auto", "deoct_engine_create", "deoct_engine_destroy",
+    "deoct_engine_attach", "deoct_engine_get_stats", "deoct_get_memory", "deoct_fit_scratch_bound",
+    "deoct_release_scratch",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -61,6 +63,12 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("eval_launches", ctypes.c_uint64),
                 ("eval_ms", ctypes.c_double), ("eval_timed", ctypes.c_uint64)]
+
+
+class EngineStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submissions", "completed", "ticks", "launches", "eval_launches", "shared_launches",
+        "max_jobs_per_launch", "max_problems_per_launch")]
 
 
 _lib = None
@@ -94,6 +102,14 @@ def load(path: str | None = None):
             "deoct_encode": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp],
             "deoct_encode_ex": [_vp, _vp, _i64, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
             "deoct_encode_auto": [_vp, _vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp],
+            "deoct_get_memory": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
+            "deoct_release_scratch": [_vp],
+            "deoct_fit_scratch_bound": [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(Params),
+                                        ctypes.POINTER(_u64)],
+            "deoct_engine_create": [ctypes.POINTER(_vp), _i32],
+            "deoct_engine_destroy": [_vp],
+            "deoct_engine_attach": [_vp, _vp],
+            "deoct_engine_get_stats": [_vp, ctypes.POINTER(EngineStats)],
             "deoct_split_values": [_vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp],
             "deoct_predict": [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
             "deoct_decode_population": [_vp, ctypes.POINTER(Dataset), _vp, _i32, _i32, _vp, _vp, _vp],
@@ -119,6 +135,33 @@ def load(path: str | None = None):
                 else ctypes.c_int
         _lib = lib
         return lib
+
+
+class Engine:
+    """Owns a ``deoct_engine``: continuous batching of the DEOCT generations of every
+    attached context's batched moving-horizon level solves in shared launches."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(load().deoct_engine_create(ctypes.byref(h), device))
+        self.handle = h
+        self.device = device
+
+    def stats(self):
+        s = EngineStats()
+        _check(load().deoct_engine_get_stats(self.handle, ctypes.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in EngineStats._fields_}
+
+    def close(self):
+        if self.handle is not None:
+            load().deoct_engine_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _check(rc):
@@ -196,6 +239,21 @@ class Context:
 
     def set_timing(self, enable: bool):
         _check(load().deoct_set_timing(self.handle, int(bool(enable))))
+
+    def memory(self):
+        """(device bytes, pinned host bytes) this context holds."""
+        d, h = _u64(), _u64()
+        _check(load().deoct_get_memory(self.handle, ctypes.byref(d), ctypes.byref(h)))
+        return int(d.value), int(h.value)
+
+    def release_scratch(self):
+        """Free the context's device scratch (synchronises the device)."""
+        _check(load().deoct_release_scratch(self.handle))
+
+    def attach_engine(self, engine):
+        """Run this context's batched level solves in `engine`'s shared launches (None detaches)."""
+        _check(load().deoct_engine_attach(self.handle, None if engine is None else engine.handle))
+        self.engine = engine
 
     def stats(self):
         s = Stats()
@@ -345,6 +403,16 @@ def deoct_eval_population(ctx: Context, ds: DeviceDataset, a, theta, depth: int,
                                         _ptr(a, 2), _ptr(theta, 4), P, depth, _ptr(counts_out, 4),
                                         _ptr(errors_out, 4), _stream(stream)))
     return counts_out, errors_out
+
+
+def fit_scratch_bound(n: int, F: int, K: int, params, rank_bytes: int = 0, ctx=None) -> int:
+    """Upper bound of the device scratch a fresh context holds after encoding an n x F set
+    and fitting it with deoct_fit_moving_horizon under `params`; with `ctx`, of what that
+    context's scratch may still grow by (no GPU call)."""
+    b = _u64()
+    _check(load().deoct_fit_scratch_bound(None if ctx is None else ctx.handle, n, F, K, rank_bytes,
+                                          ctypes.byref(params), ctypes.byref(b)))
+    return int(b.value)
 
 
 def make_params(depth, pop, gens, mut_f=0.5, cr=0.9, alpha=0.0, n_min=1, seed=0, horizon=0, flags=0):

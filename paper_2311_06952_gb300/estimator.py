@@ -80,6 +80,38 @@ class MHDEOCTClassifier:
         self._dev_tree = (a, b, torch.from_numpy(out["leaf_class"]).cuda())
         return self
 
+    def fit_tuned(self, X, y, K=None, n_grid=21, val_frac=1.0 / 3.0, split_seed=0):
+        """Complexity-parameter tuning by training, validation and retraining (the
+        procedure of the paper's Appendix C, 21 values of the parameter).
+
+        The paper does not state alpha's domain.  Here alpha = cp * e_root, with e_root
+        the misclassifications of the tree without splits on the set being fitted and cp
+        taking n_grid values evenly spaced in [0, 1] (a split must then pay for itself
+        with at least cp * e_root corrected samples).  The training set is split once
+        (seeded) into a fitting part and a validation part of val_frac (the paper's
+        50/25 split of train+validation is val_frac = 1/3); every cp is fitted on the
+        fitting part and scored on the validation part; the cp with the highest
+        validation accuracy wins, ties going to the larger cp (the simpler tree); the
+        tree is then refitted on the whole training set with that cp."""
+        Xh = np.ascontiguousarray(X if isinstance(X, np.ndarray) else X.cpu().numpy(), np.float32)
+        yh = np.ascontiguousarray(y if isinstance(y, np.ndarray) else y.cpu().numpy(), np.uint8)
+        K = int(K) if K is not None else int(yh.max()) + 1
+        fit_idx, val_idx = validation_split(len(yh), val_frac, split_seed)
+        cps = np.linspace(0.0, 1.0, n_grid)
+        e_fit = root_errors(yh[fit_idx], K)
+        acc = []
+        for cp in cps:
+            self.alpha = float(cp * e_fit)
+            self.fit(Xh[fit_idx], yh[fit_idx], K=K)
+            acc.append(self.score(Xh[val_idx], yh[val_idx]))
+        acc = np.asarray(acc)
+        best = int(np.flatnonzero(acc == acc.max())[-1])  # ties: the larger cp
+        self.alpha = float(cps[best] * root_errors(yh, K))
+        self.fit(Xh, yh, K=K)
+        self.tuning_ = dict(cp=cps, val_accuracy=acc, cp_best=float(cps[best]), alpha=self.alpha,
+                            fit_idx=fit_idx, val_idx=val_idx)
+        return self
+
     def predict(self, X):
         import torch
 
@@ -97,3 +129,15 @@ class MHDEOCTClassifier:
         _, correct = deoct.deoct_predict(self._context(), Xd, a, b, self.depth, lc,
                                          y=self._dev(y, torch.uint8))
         return int(correct.item()) / Xd.shape[0]
+
+
+def validation_split(n, val_frac, seed):
+    """Seeded split of n samples into (fitting, validation) index arrays, each sorted."""
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(n)
+    nv = int(round(n * val_frac))
+    return np.sort(perm[nv:]), np.sort(perm[:nv])
+
+
+def root_errors(y, K):
+    """Misclassifications of the tree without splits: n minus the majority class count."""
+    return int(len(y) - np.bincount(y, minlength=K).max())

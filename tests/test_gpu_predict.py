@@ -98,3 +98,54 @@ def test_estimator_paper_defaults_run_and_match_oracle(c):
     np.testing.assert_array_equal(clf.tree_["a"].astype(np.int32), ref["a"])
     np.testing.assert_array_equal(clf.tree_["theta"], ref["theta"])
     np.testing.assert_array_equal(clf.tree_["leaf_class"], ref["leaf_class"])
+
+
+def _oracle_tuned(X, y, K, depth, horizon, P, G, seed, n_grid=21, val_frac=1.0 / 3.0, split_seed=0):
+    """The training-validation-retraining procedure of Appendix C restated on the oracle:
+    alpha = cp * (n - majority count) of the set being fitted, cp on an even grid of
+    [0, 1]; validation accuracy of the tree routed on raw values; ties to the larger cp."""
+    perm = np.random.Generator(np.random.PCG64(split_seed)).permutation(len(y))
+    nv = int(round(len(y) * val_frac))
+    fit_idx, val_idx = np.sort(perm[nv:]), np.sort(perm[:nv])
+
+    def mh(Xs, ys, alpha):
+        ranks, nu = oracle.encode(Xs)
+        t = oracle.mh(ranks, nu, ys, K, depth=depth, horizon=horizon, P=P, G=G, alpha=alpha, seed=seed,
+                      cart_seeds=True, de_seeds=True)
+        return t, oracle.split_values(Xs, t["a"], t["theta"])
+
+    def e_root(ys):
+        return len(ys) - np.bincount(ys, minlength=K).max()
+
+    cps = np.linspace(0.0, 1.0, n_grid)
+    acc = []
+    for cp in cps:
+        t, b = mh(X[fit_idx], y[fit_idx], float(cp * e_root(y[fit_idx])))
+        pred = oracle.predict(X[val_idx], t["a"], b, depth, t["leaf_class"])
+        acc.append(np.mean(pred == y[val_idx]))
+    acc = np.asarray(acc)
+    best = int(np.flatnonzero(acc == acc.max())[-1])
+    t, _ = mh(X, y, float(cps[best] * e_root(y)))
+    return cps[best], acc, t
+
+
+def test_alpha_tuning_selects_what_the_oracle_selects():
+    """Appendix C's procedure on a small noisy set: the GPU estimator and the oracle score
+    every cp identically, pick the same one and refit the same tree."""
+    from paper_2311_06952_gb300.estimator import MHDEOCTClassifier
+    rng = _rng(91)
+    n, F, K, depth = 1500, 5, 2, 4
+    X = np.round(rng.normal(size=(n, F)), 2).astype(np.float32)
+    # one planted split under 35% label noise: deeper splits only fit noise, several cp
+    # values tie on validation and the largest of them must win
+    y = datagen.flip_labels(datagen.planted_tree_labels(X, 1, K, rng), K, 0.35, rng)
+    clf = MHDEOCTClassifier(depth=depth, horizon=2, pop=16, gens=12, cr=0.9, dither=False, seed=4,
+                            warm_starts=("cart", "deoct"))
+    clf.fit_tuned(X, y, K=K)
+    cp, acc, tree = _oracle_tuned(X, y, K, depth, 2, 16, 12, 4)
+    np.testing.assert_array_equal(clf.tuning_["val_accuracy"], acc)
+    assert clf.tuning_["cp_best"] == cp
+    assert cp > 0.0  # the noise makes some pruning pay on validation data
+    np.testing.assert_array_equal(clf.tree_["a"].astype(np.int32), tree["a"])
+    np.testing.assert_array_equal(clf.tree_["theta"], tree["theta"])
+    np.testing.assert_array_equal(clf.tree_["leaf_class"], tree["leaf_class"])

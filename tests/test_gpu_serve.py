@@ -1,57 +1,136 @@
-"""Serving on the GPU: each request's tree is the same alone and in the mix
-(exact: per-request data, parameters and Philox seeds), with requests running
-concurrently on their slots' streams."""
+"""Serving on the GPU.
+
+- Every served tree equals the oracle's moving-horizon tree for that request
+  (Algorithm 2, same data, parameters and Philox seed) and the same request fitted
+  alone, whether the requests share the engine's launches or run on their own streams.
+- With the engine, launches carry the work of several requests at once.
+- The library's scratch bound covers what a context really holds after a fit, and the
+  server's charge never exceeds its budget."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2311_06952_gb300 import datagen, serve
 
 pytestmark = pytest.mark.gpu
 
 
-def _requests(num=8, seed=77):
-    reqs = datagen.serving_requests(num=num, rate=200.0, seed=seed, n_range=(2_000, 40_000),
-                                    materialize=True)
+def _requests(num=8, seed=77, n_range=(2_000, 20_000), pop=32, gens=80):
+    reqs = datagen.serving_requests(num=num, rate=200.0, seed=seed, n_range=n_range, materialize=True)
     out = []
     for r in reqs:
         out.append(serve.FitRequest(X=r["X"], y=r["y"], K=r["K"], depth=r["depth"],
-                                    horizon=r["horizon"], pop=32, gens=12, seed=r["id"], id=r["id"],
+                                    horizon=r["horizon"], pop=pop, gens=gens, seed=r["id"], id=r["id"],
                                     arrival=r["arrival"]))
     return out
 
 
-def test_alone_equals_in_the_mix():
-    import torch
-    from paper_2311_06952_gb300 import build, deoct
+def _oracle_tree(r):
+    old = oracle.set_threads(oracle.host_cores())
+    try:
+        ranks, nu = oracle.encode_omp(r.X)
+        return oracle.mh(ranks, nu, r.y, r.K, depth=r.depth, horizon=r.horizon, P=r.pop, G=r.gens,
+                         M=r.mut_f, CR=r.cr, seed=r.seed)
+    finally:
+        oracle.set_threads(old)
+
+
+@pytest.fixture(scope="module")
+def reqs():
+    from paper_2311_06952_gb300 import build
     build.build()
-    reqs = _requests()
-    ctx = deoct.Context(0)
-    stream = torch.cuda.Stream()
-    alone = {}
-    for r in reqs:
-        with torch.cuda.stream(stream):
-            alone[r.id] = serve.fit_on_stream(ctx, r, stream)
-    ctx.close()
-    srv = serve.Server(budget_bytes=64 << 30, slots=4)
-    mixed = serve.run_trace(srv, reqs)
-    srv.close()
-    assert srv.max_concurrent >= 2  # work of several requests was in flight together
-    for res in mixed:
-        ref = alone[res.id]
-        for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
-            np.testing.assert_array_equal(getattr(res, k), ref[k], err_msg="request %d %s" % (res.id, k))
+    rs = _requests()
+    return rs, {r.id: _oracle_tree(r) for r in rs}
 
 
-def test_plain_and_batched_requests_agree():
+def _check(res, ref):
+    for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
+        np.testing.assert_array_equal(np.asarray(getattr(res, k)).astype(ref[k].dtype), ref[k],
+                                      err_msg="request %d %s" % (res.id, k))
+
+
+def test_alone_equals_oracle(reqs):
     import torch
     from paper_2311_06952_gb300 import deoct
-    r = _requests(num=1, seed=5)[0]
+    rs, ref = reqs
     ctx = deoct.Context(0)
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        a = serve.fit_on_stream(ctx, r, s)
-        r.batched = False
-        b = serve.fit_on_stream(ctx, r, s)
+    stream = torch.cuda.Stream()
+    for r in rs:
+        with torch.cuda.stream(stream):
+            out = serve.fit_on_stream(ctx, r, stream)
+        for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
+            np.testing.assert_array_equal(out[k].astype(ref[r.id][k].dtype), ref[r.id][k])
     ctx.close()
-    for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
-        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("engine", [True, False])
+def test_served_trees_equal_the_oracle_in_the_mix(reqs, engine):
+    rs, ref = reqs
+    budget = 64 << 30
+    srv = serve.Server(budget_bytes=budget, slots=4, engine=engine)
+    try:
+        mixed = serve.run_trace(srv, rs)
+        st = srv.engine_stats()
+    finally:
+        srv.close()
+    assert srv.max_concurrent >= 2  # several requests were resident together
+    for res in mixed:
+        _check(res, ref[res.id])
+        assert res.scratch_after - res.scratch_before <= res.scratch_reserve <= res.scratch_bound
+    assert srv.peak_charged <= budget
+    assert srv.charged == sum(srv.retained)
+    if engine:
+        assert st["completed"] == st["submissions"] > 0
+        assert st["shared_launches"] > 0 and st["max_jobs_per_launch"] >= 2, st
+
+
+def test_engine_mixes_rank_widths_depths_and_classes():
+    """Requests of both rank widths, subtree depths 2 and 3 and different K, F and n in one
+    engine; the first three share rank width, subtree depth and size class but not K or F,
+    so their problems run in the same launches.  Each tree equals the oracle's."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    rs = []
+    for i, (n, F, K, depth, horizon, wide) in enumerate([
+            (9000, 5, 2, 4, 2, False), (11000, 9, 5, 3, 2, False), (10000, 4, 3, 4, 2, False),
+            (70000, 4, 3, 3, 3, True), (20000, 6, 2, 5, 3, True)]):
+        X = (rng.random((n, F)) if wide else np.round(rng.random((n, F)), 3)).astype(np.float32)
+        y = datagen.planted_tree_labels(X, 3, K, rng)
+        rs.append(serve.FitRequest(X=X, y=y, K=K, depth=depth, horizon=horizon, pop=24, gens=60, seed=40 + i,
+                                   id=i, arrival=0.0))
+    srv = serve.Server(budget_bytes=64 << 30, slots=5, engine=True)
+    try:
+        res = serve.run_trace(srv, rs)
+        st = srv.engine_stats()
+    finally:
+        srv.close()
+    for r, q in zip(sorted(res, key=lambda x: x.id), rs):
+        _check(r, _oracle_tree(q))
+    assert st["max_jobs_per_launch"] >= 2
+
+
+@pytest.mark.parametrize("case", [
+    # n, F, K, depth, horizon, pop, flags
+    (50_000, 12, 3, 6, 3, 64, "batched"),
+    (30_000, 30, 7, 4, 2, 32, "plain"),
+    (70_000, 5, 2, 5, 3, 40, "batched+seeds"),
+    (4_000, 60, 10, 6, 3, 128, "batched"),
+])
+def test_scratch_bound_covers_a_fresh_context(case):
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    n, F, K, depth, horizon, pop, kind = case
+    rng = np.random.Generator(np.random.PCG64(n + F))
+    X = rng.random((n, F)).astype(np.float32)
+    y = datagen.planted_tree_labels(X, min(depth, 4), K, rng)
+    flags = 0 if kind == "plain" else deoct.DEOCT_BATCHED
+    if "seeds" in kind:
+        flags |= deoct.DEOCT_CART_SEEDS | deoct.DEOCT_DE_SEEDS
+    prm = deoct.make_params(depth, pop, 3, horizon=horizon, flags=flags)
+    ctx = deoct.Context(0)
+    ds = deoct.encode_dataset(ctx, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), K, 0)
+    deoct.deoct_fit_moving_horizon(ctx, ds, prm)
+    held, _ = ctx.memory()
+    ctx.close()
+    bound = deoct.fit_scratch_bound(n, F, K, prm)
+    assert held <= bound, (held, bound)
+    assert held >= bound // 8  # the bound is not vacuous

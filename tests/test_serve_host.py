@@ -42,9 +42,13 @@ def test_slots_bound_concurrency():
     assert srv.max_concurrent == 3
 
 
+def _cost(req):
+    return serve.input_bytes(*req.X.shape) + serve.scratch_bound(req)
+
+
 def test_budget_serialises_and_fifo():
     log = []
-    fp = serve.footprint_bytes(1000, 4, 3, 16, 2)
+    fp = _cost(_req(0))
     srv = serve.Server(budget_bytes=int(fp * 1.5), slots=4, fit_fn=_fake_fit(0.02, log))
     res = serve.run_trace(srv, [_req(i) for i in range(5)])
     srv.close()
@@ -56,7 +60,7 @@ def test_budget_serialises_and_fifo():
 
 
 def test_over_budget_request_is_rejected_not_queued():
-    small = serve.footprint_bytes(10, 1, 1, 16, 2)
+    small = _cost(_req(1, n=10, F=1, depth=1))
     srv = serve.Server(budget_bytes=2 * small, slots=2, fit_fn=_fake_fit(0.0, []))
     fut = srv.submit(_req(0, n=100000, F=50))
     with pytest.raises(MemoryError):
@@ -71,3 +75,54 @@ def test_sequential_queue_latencies():
     assert np.allclose(lat, [1.0, 1.9, 2.8])
     st = serve.latency_stats([1.0, 2.0, 3.0, 4.0])
     assert st["p50_s"] == 2.5
+
+
+def test_retained_scratch_is_charged_and_reused():
+    """A slot keeps the scratch its request grew; the budget is charged with it, and a
+    later request on that slot is charged only the growth it may still need."""
+    grown = {}
+
+    def fit(slot, req):
+        B = (1 << req.depth) - 1
+        grown[slot] = max(grown.get(slot, 0), serve.scratch_bound(req) // 2)  # what the fit kept
+        return dict(a=np.zeros(B, np.uint16), theta=np.zeros(B, np.uint32),
+                    leaf_class=np.zeros(B + 1, np.uint8), kind=np.zeros(B, np.int32),
+                    node_fit=np.zeros(B), scratch_bytes=grown[slot])
+    def growth(slot, req):  # what the fake fit may still grow the slot by
+        return max(0, serve.scratch_bound(req) // 2 - grown.get(slot, 0))
+    big = _req(0, n=20000, F=8)
+    budget = _cost(big) + serve.input_bytes(20000, 8) + 1
+    srv = serve.Server(budget_bytes=budget, slots=2, fit_fn=fit, growth_fn=growth)
+    res = serve.run_trace(srv, [_req(i, n=20000, F=8) for i in range(4)])
+    srv.close()
+    assert srv.peak_charged <= budget
+    # after the first request a slot holds half the bound: the next ones fit beside it
+    assert srv.retained == [grown.get(0, 0), grown.get(1, 0)]
+    assert srv.charged == sum(srv.retained)
+    for r in res:
+        assert r.scratch_after - r.scratch_before <= r.scratch_reserve
+        assert r.footprint == r.inputs + (r.scratch_after - r.scratch_before)
+
+
+def test_admission_prefers_the_slot_that_already_holds_scratch():
+    def fit(slot, req):
+        B = (1 << req.depth) - 1
+        return dict(a=np.zeros(B, np.uint16), theta=np.zeros(B, np.uint32),
+                    leaf_class=np.zeros(B + 1, np.uint8), kind=np.zeros(B, np.int32),
+                    node_fit=np.zeros(B), scratch_bytes=serve.scratch_bound(req))
+    held = {}
+
+    def fit2(slot, req):
+        out = fit(slot, req)
+        held[slot] = out["scratch_bytes"]
+        return out
+
+    def growth(slot, req):
+        return max(0, serve.scratch_bound(req) - held.get(slot, 0))
+    r0 = _req(0, n=5000, F=6)
+    budget = _cost(r0) + serve.input_bytes(5000, 6)  # room for one more request's inputs only
+    srv = serve.Server(budget_bytes=budget, slots=3, fit_fn=fit2, growth_fn=growth)
+    res = serve.run_trace(srv, [_req(i, n=5000, F=6, arrival=0.01 * i) for i in range(3)])
+    srv.close()
+    assert len({r.slot for r in res}) == 1  # every request reused the first slot's scratch
+    assert srv.peak_charged <= budget
