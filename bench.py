@@ -45,11 +45,12 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
 # headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
 # left out.
-EVAL_TRAFFIC = {"source_sha256_16": "a4c4dbcf0c09479c", "bytes": 362_880_256 + 3_740_160,
+EVAL_TRAFFIC = {"source_sha256_16": "783cce14f60f868c", "bytes": 352_830_720 + 3_484_416,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
-                "ncu": {"inst_per_cycle": 3.336, "issue_frac": 3.336 / 4.0, "alu_pipe_frac": 0.7720,
-                        "shared_pipe_frac": 0.810, "inst_per_chunk": 35.46, "dram_gbs": 33.8,
-                        "dram_frac_of_peak": 0.0051}}
+                "ncu": {"inst_per_cycle": 3.336, "issue_frac": 0.8348, "alu_pipe_frac": 0.7720,
+                        "shared_pipe_frac": 2773944851 / 152 / (10.88448e-3 * 2.07e9),
+                        "inst_per_chunk": 35.46, "dram_gbs": (352_830_720 + 3_484_416) / 10.88448e-3 / 1e9,
+                        "dram_frac_of_peak": (352_830_720 + 3_484_416) / 10.88448e-3 / 1e9 / 6777.3}}
 
 
 def _strip_comments(src):
