@@ -129,6 +129,13 @@ DEOCT_API int deoct_reset_stats(deoct_ctx* ctx);
  * DEOCT_ERR_INVALID; a shape whose tile does not fit in shared memory fails at
  * the next evaluation. */
 DEOCT_API int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, int32_t grid);
+/* deoct_set_eval_streaming: with on != 0, every ballot-mode evaluation of
+ * `ctx` (2^depth K <= 128) runs on the streaming kernel -- a producer warp
+ * stages tiles into a ring of landing zones for the routing warps -- also for
+ * groups of 16 or more trees, where the automatic choice is the re-laid kernel
+ * (the batched level solve measures both).  Results are unchanged; 0 restores
+ * the automatic choice.  sync. */
+DEOCT_API int deoct_set_eval_streaming(deoct_ctx* ctx, int32_t on);
 
 /* Self-test of the library's failure detection (no counterpart in the paper).
  * Every device-side wait of the library (the evaluator's mbarrier waits) is

@@ -455,6 +455,14 @@ int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, 
   API_END
 }
 
+int deoct_set_eval_streaming(deoct_ctx* ctx, int32_t on) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  ctx->force_stream = on ? 1 : 0;
+  return DEOCT_OK;
+  API_END
+}
+
 namespace deoct {
 namespace {
 // One warp waits on an mbarrier that nothing arrives on: lane 0's bounded wait

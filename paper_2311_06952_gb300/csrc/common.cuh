@@ -100,9 +100,10 @@ struct deoct_ctx {
   double eval_ms = 0.0;
   uint64_t eval_timed = 0;
   // evaluator shapes picked by the autotuner, keyed by workload class
-  std::vector<std::pair<uint64_t, std::array<int, 3>>> tuned;
+  std::vector<std::pair<uint64_t, std::array<int, 4>>> tuned;  // S, TG, warps, stream
   // evaluator launch shape forced by deoct_set_eval_config (0 = automatic)
   int force_S = 0, force_TG = 0, force_warps = 0, force_grid = 0;
+  int force_stream = 0;  // deoct_set_eval_streaming: streaming kernel for every ballot launch
   // shared engine that runs the generations of this context's batched level
   // solves together with other contexts' (deoct_engine_attach; nullable)
   deoct_engine* engine = nullptr;

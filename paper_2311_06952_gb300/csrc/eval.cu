@@ -320,7 +320,10 @@ static int eval_mode(int D, int K) { return ((1 << D) * K <= 32 * kQMax && D <= 
 // single landing zone leaves room for twice the tile of the streaming ring
 // (measured on GB300: HIGGS-shaped uint32 data, F = 28, ran 1.6x slower on the
 // ring's smaller tiles).
-static bool use_stream(int mode, int W, int TG) { (void)W; return mode == 0 && TG < 16; }
+static bool use_stream(int mode, int W, int TG, int force = 0) {
+  (void)W;
+  return mode == 0 && (TG < 16 || force);
+}
 
 // Landing zones the streaming kernel wants: three for small groups (HBM-bound),
 // two for 16+ trees (the next tile flies while this one is routed).
@@ -330,8 +333,8 @@ static int want_stages(int TG) { return TG < 16 ? kMaxStages : 2; }
 // (0: as many as it wants; the re-laid kernel always has its tile and one
 // landing zone).
 static size_t eval_smem(int mode, int W, int D, int S, int TG, int F, int K, int warps,
-                        int nstage = 0, int lab_stage = 1) {
-  if (use_stream(mode, W, TG))
+                        int nstage = 0, int lab_stage = 1, int force_stream = 0) {
+  if (use_stream(mode, W, TG, force_stream))
     return stream_layout(W, D, S, TG, F, K, nstage ? nstage : want_stages(TG), lab_stage).total;
   return smem_layout(mode, W, D, S, TG, F, K, warps, lab_stage).total;
 }
@@ -414,6 +417,7 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
   if (ctx->force_TG) c.TG = std::min(ctx->force_TG, std::max(1, P));
   if (ctx->force_warps) c.warps = ctx->force_warps;
   if (ctx->force_grid) c.grid = ctx->force_grid;
+  if (ctx->force_stream) c.stream = 1;
   return c;
 }
 
@@ -497,11 +501,11 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
   // zones for small groups, two otherwise) that keeps two CTAs per SM, else
   // the deepest that fits one CTA; forced shapes that fit in no other way
   // drop the label landing zones (labels then come by plain loads).
-  const bool streaming = use_stream(mode, W, cfg.TG);
+  const bool streaming = use_stream(mode, W, cfg.TG, cfg.stream);
   const size_t cap = (size_t)ctx->max_smem_optin - 1024;  // room for the static shared memory
   const size_t two_per_sm = std::min(cap, (size_t)(ctx->smem_per_sm - 2 * 1024) / 2);
   auto need = [&](int ns, int lab) {
-    return eval_smem(mode, W, D, cfg.S, cfg.TG, plan.Fmax, plan.Kmax, cfg.warps, ns, lab);
+    return eval_smem(mode, W, D, cfg.S, cfg.TG, plan.Fmax, plan.Kmax, cfg.warps, ns, lab, cfg.stream);
   };
   const int want = streaming ? want_stages(cfg.TG) : 1;
   a.nstage = 0;

@@ -40,6 +40,7 @@ struct EvalConfig {
   int TG = 256;     // trees per job
   int warps = 8;    // warps per CTA
   int grid = 0;     // CTAs (0: chosen from occupancy)
+  int stream = 0;   // 1: the streaming kernel also for groups of 16+ trees (ballot mode)
 };
 
 // Evaluate several problems that share rank width W and depth D.  Either pass

@@ -611,9 +611,10 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
       cfg.S = kv.second[0];
       cfg.TG = kv.second[1];
       cfg.warps = kv.second[2];
+      cfg.stream = kv.second[3];
       have = true;
     }
-  const bool forced = ctx->force_S || ctx->force_TG || ctx->force_warps || ctx->force_grid;
+  const bool forced = ctx->force_S || ctx->force_TG || ctx->force_warps || ctx->force_grid || ctx->force_stream;
   if (!have && !forced) {
     // candidates around the heuristic; each runs the real evaluation of S^1
     std::vector<EvalConfig> cands;
@@ -629,6 +630,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
         for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG);
         if (!dup) cands.push_back(x);
       }
+
     cudaEvent_t e0, e1;
     DEOCT_CUDA_TRY(cudaEventCreate(&e0));
     DEOCT_CUDA_TRY(cudaEventCreate(&e1));
@@ -660,7 +662,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cfg = best;
-    ctx->tuned.push_back({key, {cfg.S, cfg.TG, cfg.warps}});
+    ctx->tuned.push_back({key, {cfg.S, cfg.TG, cfg.warps, cfg.stream}});
     for (int m = 0; m < M; ++m)
       DEOCT_CUDA_TRY(cudaMemsetAsync(dp[m].counts, 0, (size_t)P * L * K * 4, s));
   }

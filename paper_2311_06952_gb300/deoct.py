@@ -36,7 +36,7 @@ EXPORTED = [
     "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
     "deoct_selftest_wait", "deoct_encode_auto", "deoct_engine_create", "deoct_engine_destroy",
     "deoct_engine_attach", "deoct_engine_get_stats", "deoct_get_memory", "deoct_fit_scratch_bound",
-    "deoct_release_scratch",
+    "deoct_release_scratch", "deoct_set_eval_streaming",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -104,6 +104,7 @@ def load(path: str | None = None):
             "deoct_encode_auto": [_vp, _vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp],
             "deoct_get_memory": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
             "deoct_release_scratch": [_vp],
+            "deoct_set_eval_streaming": [_vp, _i32],
             "deoct_fit_scratch_bound": [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(Params),
                                         ctypes.POINTER(_u64)],
             "deoct_engine_create": [ctypes.POINTER(_vp), _i32],
@@ -273,6 +274,10 @@ class Context:
     def set_eval_config(self, S=0, TG=0, warps=0, grid=0):
         """Force the evaluator's launch shape (0 = automatic); results are unchanged."""
         _check(load().deoct_set_eval_config(self.handle, S, TG, warps, grid))
+
+    def set_eval_streaming(self, on: bool):
+        """Run every ballot-mode evaluation on the streaming kernel (results unchanged)."""
+        _check(load().deoct_set_eval_streaming(self.handle, int(bool(on))))
 
 
 class DeviceDataset:

@@ -193,3 +193,22 @@ def test_moving_horizon_edge_shapes(c, depth, horizon, F, n_min):
         np.testing.assert_array_equal(out["theta"], ref["theta"])
         np.testing.assert_array_equal(out["kind"], ref["kind"])
         np.testing.assert_array_equal(out["leaf_class"], ref["leaf_class"])
+
+
+def test_moving_horizon_streaming_kernel_forced_bit_exact(c):
+    """The batched level solve with the streaming kernel for every evaluation: same tree."""
+    from paper_2311_06952_gb300 import deoct
+    X, y, K, kw, rb = _mh_case("w2_small")
+    ds = gpu_dataset(c, X, y, K, rb)
+    ranks, nu = oracle.encode(X)
+    ref = oracle.mh(ranks, nu, y, K, depth=kw["depth"], horizon=kw["horizon"], P=kw["P"], G=kw["G"],
+                    seed=kw["seed"])
+    prm = deoct.make_params(kw["depth"], kw["P"], kw["G"], seed=kw["seed"], horizon=kw["horizon"],
+                            flags=deoct.DEOCT_BATCHED)
+    try:
+        c.set_eval_streaming(True)
+        out = deoct.deoct_fit_moving_horizon(c, ds, prm)
+    finally:
+        c.set_eval_streaming(False)
+    for k in ("kind", "a", "theta", "node_fit", "leaf_class"):
+        np.testing.assert_array_equal(out[k].astype(ref[k].dtype), ref[k], err_msg=k)

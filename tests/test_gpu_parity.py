@@ -180,6 +180,38 @@ def test_eval_launch_shapes_bit_exact(c, shape):
         c.set_eval_config(0, 0, 0, 0)
 
 
+@pytest.mark.parametrize("shape", [(0, 0, 0, 0), (256, 128, 16, 0), (512, 64, 16, 7), (1024, 16, 6, 3),
+                                   (128, 200, 16, 2)])
+@pytest.mark.parametrize("depth,K", [(3, 4), (4, 2), (2, 30), (5, 3)])
+def test_eval_streaming_kernel_large_groups_bit_exact(c, shape, depth, K):
+    """The streaming kernel forced for groups of 16+ trees (shared class masks, trees split over
+    the routing warps, two landing zones): same counts, both rank widths, full set and subset."""
+    from paper_2311_06952_gb300 import deoct
+    S, TG, warps, grid = shape
+    rng = _rng(600 + S + depth * 7 + K)
+    n, F, P = 30011, 7, 200
+    X = np.round(rng.random((n, F)), 3).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth)
+    idx = np.sort(rng.choice(n, n // 3, replace=False)).astype(np.int32)
+    ref_sub = oracle.eval_counts(ranks, y, K, a, th, depth, idx=idx)
+    try:
+        c.set_eval_streaming(True)
+        c.set_eval_config(S, TG, warps, grid)
+        for rb in (2, 4):
+            ds = gpu_dataset(c, X, y, K, rb)
+            counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth)
+            np.testing.assert_array_equal(u32(counts), ref)
+            counts, _ = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth,
+                                                    sample_idx=to_dev(idx))
+            np.testing.assert_array_equal(u32(counts), ref_sub)
+    finally:
+        c.set_eval_streaming(False)
+        c.set_eval_config(0, 0, 0, 0)
+
+
 @pytest.mark.parametrize("shape", [(0, 0, 0, 0), (128, 2, 16, 3), (1024, 8, 16, 5), (512, 1, 4, 1)])
 @pytest.mark.parametrize("depth,K", [(7, 3), (4, 29)])
 def test_eval_shared_atomic_mode_shapes_bit_exact(c, shape, depth, K):
