@@ -382,6 +382,13 @@ def serve_compare(num, slots):
     ctx.close()
     seq_lat = serve.sequential_queue_latencies([r["arrival"] for r in raw], service)
     seq_makespan = max(a + l for a, l in zip([r["arrival"] for r in raw], seq_lat))
+    # the same requests arriving 10x faster (200 req/s): the GPU saturates and the requests'
+    # work queues; served with the engine and with a stream per request
+    burst = [dict(r, arrival=r["arrival"] / 10.0) for r in raw]
+    res_be, beng = _serve_trace(burst, slots, True)
+    res_bs, bstr = _serve_trace(burst, slots, False)
+    same = same and all(np.array_equal(getattr(r, k), getattr(by_e[r.id], k)) for r in res_be + res_bs
+                        for k in keys)
     return {"metric": "p50/p99 request latency and requests/s", "workload": SERVE_WORKLOAD,
             "requests": num, "served_engine": eng, "served_streams": strm,
             "sequential_plain": {"latency": serve.latency_stats(seq_lat),
@@ -390,6 +397,11 @@ def serve_compare(num, slots):
             "engine_vs_streams": {"p99": eng["latency"]["p99_s"] / strm["latency"]["p99_s"],
                                   "p50": eng["latency"]["p50_s"] / strm["latency"]["p50_s"],
                                   "throughput": eng["throughput_rps"] / strm["throughput_rps"]},
+            "burst_200rps": {"served_engine": beng, "served_streams": bstr,
+                             "engine_vs_streams": {
+                                 "p99": beng["latency"]["p99_s"] / bstr["latency"]["p99_s"],
+                                 "p50": beng["latency"]["p50_s"] / bstr["latency"]["p50_s"],
+                                 "throughput": beng["throughput_rps"] / bstr["throughput_rps"]}},
             "identical_trees_engine_streams_plain": bool(same), "data": "synthetic"}
 
 
