@@ -708,19 +708,34 @@ def run_ours(args):
     B = (1 << D) - 1
     d2h = B * 2 + B * 4 + 8
 
-    def e2e_step(sid):
-        Xg = Xh.to("cuda", non_blocking=True)
-        yg = yh.to("cuda", non_blocking=True)
-        r_, nu_ = deoct.deoct_encode(ctx, Xg, 2)
-        ds = deoct.DeviceDataset(r_, 2, nu_, yg, n, F, K)
-        return deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)  # host outputs (sync)
+    # every step copies its inputs host -> device and reads its fitted tree back; the copy of
+    # step i + 1 runs on a copy stream while step i computes (two device buffers in turn)
+    copy_stream = torch.cuda.Stream()
+    bufX = [torch.empty_like(Xh, device="cuda") for _ in range(2)]
+    bufY = [torch.empty_like(yh, device="cuda") for _ in range(2)]
+    landed = [torch.cuda.Event() for _ in range(2)]
 
-    e2e_step(multirank.stream_id(rank))
+    def load(i):
+        with torch.cuda.stream(copy_stream):
+            bufX[i % 2].copy_(Xh, non_blocking=True)
+            bufY[i % 2].copy_(yh, non_blocking=True)
+            landed[i % 2].record(copy_stream)
+
+    def e2e_steps(k, sid):
+        load(0)
+        for i in range(k):
+            stream.wait_event(landed[i % 2])
+            if i + 1 < k:
+                load(i + 1)  # the previous user of this buffer (step i - 1) has finished
+            r_, nu_ = deoct.deoct_encode(ctx, bufX[i % 2], 2)
+            ds = deoct.DeviceDataset(r_, 2, nu_, bufY[i % 2], n, F, K)
+            deoct.deoct_fit_subtree(ctx, ds, prm, stream_id=sid)  # host outputs (sync)
+
+    e2e_steps(1, multirank.stream_id(rank))
     multirank.barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        e2e_step(multirank.stream_id(rank))
+    e2e_steps(args.steps, multirank.stream_id(rank))
     torch.cuda.synchronize()
     t_e2e = multirank.max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_value = multirank.whole_job_rate(evals_per_step, world, t_e2e / args.steps)
@@ -766,7 +781,10 @@ def run_ours(args):
                                   "frac": hbm_achieved / peaks["hbm_gbs"],
                                   "algorithmic_bytes_per_launch": bytes_per_launch,
                                   "peak_kind": peak_kind}},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pipeline": "each step's X, y copied from pinned host memory inside the timed region; "
+                            "step i + 1's copy on a copy stream while step i runs; the fitted tree "
+                            "read back to the host every step"},
         "clocks": clocks,
         "result": {"fitness": res[2], "train_accuracy": 1.0 - res[2] / n},
     }
