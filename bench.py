@@ -45,7 +45,7 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
 # headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
 # left out.
-EVAL_TRAFFIC = {"source_sha256_16": "783cce14f60f868c", "bytes": 352_830_720 + 3_484_416,
+EVAL_TRAFFIC = {"source_sha256_16": "db15e346de12242c", "bytes": 352_830_720 + 3_484_416,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 0.8348, "alu_pipe_frac": 0.7720,
                         "shared_pipe_frac": 2773944851 / 152 / (10.88448e-3 * 2.07e9),
@@ -78,8 +78,10 @@ def _strip_comments(src):
 
 
 def _eval_source_hash():
-    """Key of the evaluator kernel's code: the `eval_kernel` template of csrc/eval.cu and
-    the headers it is built from, comments and whitespace left out."""
+    """Key of the evaluator kernel's code: the `eval_kernel` template of csrc/eval.cu, the
+    kernel header csrc/eval_kernel.cuh and the device helpers of csrc/common.cuh (from its
+    "device helpers" section on: the host-side context and error code above it are not the
+    kernel's), comments and whitespace left out."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2311_06952_gb300", "csrc")
     ev = open(os.path.join(csrc, "eval.cu")).read()
@@ -87,9 +89,11 @@ def _eval_source_hash():
     a = ev.rindex("template", 0, a)
     b = ev.index("int launch_t(", a)
     h = hashlib.sha256(_strip_comments(ev[a:b]).encode())
-    for f in ("eval_kernel.cuh", "common.cuh"):
-        with open(os.path.join(csrc, f)) as fh:
-            h.update(_strip_comments(fh.read()).encode())
+    with open(os.path.join(csrc, "eval_kernel.cuh")) as fh:
+        h.update(_strip_comments(fh.read()).encode())
+    with open(os.path.join(csrc, "common.cuh")) as fh:
+        common = fh.read()
+    h.update(_strip_comments(common[common.index("// device helpers"):]).encode())
     return h.hexdigest()[:16]
 
 

@@ -56,3 +56,18 @@ def test_traffic_is_null_for_other_code(tmp_path, monkeypatch):
     common.write_text(common.read_text() + "\nnamespace deoct { constexpr int kChanged = 1; }\n")
     assert bench._traffic_default() is None
     assert bench._ncu_default() is None
+
+
+def test_source_key_covers_the_device_helpers_only(tmp_path, monkeypatch):
+    """common.cuh's host-side context and error codes are not the kernel's code; its device
+    helpers are."""
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", root)
+    base = bench._eval_source_hash()
+    common = csrc / "common.cuh"
+    text = common.read_text()
+    common.write_text(text.replace("  int device = 0;", "  int device = 0;\n  int unrelated_host_field = 0;", 1))
+    assert bench._eval_source_hash() == base
+    common.write_text(text.replace("return (uint32_t)(((uint64_t)x * (uint64_t)m) >> 32);",
+                                   "return (uint32_t)(((uint64_t)x * (uint64_t)m) >> 31);", 1))
+    assert bench._eval_source_hash() != base
