@@ -638,23 +638,31 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
     EvalConfig best = cfg;
     const int saved_timing = ctx->timing;
     ctx->timing = 0;
+    // the best of three timings per candidate: a single cold launch misranked
+    // shapes that differ by a few percent (measured on GB300)
     for (const EvalConfig& x : cands) {
       DEOCT_TRY(build_plan(ctx, &be, x, F, K, P, s));
-      for (int m = 0; m < M; ++m)
-        DEOCT_CUDA_TRY(cudaMemsetAsync(dp[m].counts, 0, (size_t)P * L * K * 4, s));
-      DEOCT_CUDA_TRY(cudaEventRecord(e0, s));
-      int rc = eval_launch(ctx, W, Dt, be.plan, x, s);
-      DEOCT_CUDA_TRY(cudaEventRecord(e1, s));
-      if (rc != DEOCT_OK) {
-        clear_error();
-        cudaGetLastError();
-        continue;
+      float ms_x = 1e30f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        for (int m = 0; m < M; ++m)
+          DEOCT_CUDA_TRY(cudaMemsetAsync(dp[m].counts, 0, (size_t)P * L * K * 4, s));
+        DEOCT_CUDA_TRY(cudaEventRecord(e0, s));
+        int rc = eval_launch(ctx, W, Dt, be.plan, x, s);
+        DEOCT_CUDA_TRY(cudaEventRecord(e1, s));
+        if (rc != DEOCT_OK) {
+          clear_error();
+          cudaGetLastError();
+          ok = false;
+          break;
+        }
+        DEOCT_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        DEOCT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        ms_x = std::min(ms_x, ms);
       }
-      DEOCT_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0;
-      DEOCT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
-        best_ms = ms;
+      if (ok && ms_x < best_ms) {
+        best_ms = ms_x;
         best = x;
       }
     }
