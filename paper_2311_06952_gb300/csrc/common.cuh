@@ -276,7 +276,25 @@ __device__ __forceinline__ uint32_t pack_node(int a, uint32_t theta) {
   return a == 0 ? 0u : ((uint32_t)(a - 1) << 24) | (theta & kThetaMask);
 }
 
-// Decode one gene pair (Eq. aenc / Eq. benc in rank form).
+// floor(bhat * N) clamped to [0, N - 1], for N = n_p + 1 <= 2^24 + 1, in
+// integers.  A finite bhat in [0, 1) is m 2^-s with a 24-bit significand m and
+// s >= 24, so bhat N = m N 2^-s exactly (m N < 2^49) and its floor is
+// (m N) >> s; negative values (and -0) give 0, values >= 1 and +inf give N - 1,
+// NaN gives 0.  The same value as floor of the exact double product, clamped,
+// without FP64 arithmetic (a slow pipe on this GPU).
+__device__ __forceinline__ uint32_t floor_times(float bhat, uint32_t N) {
+  const uint32_t b = __float_as_uint(bhat);
+  if (b >> 31) return 0u;                                   // negative, -0
+  if (b >= 0x7F800000u) return b == 0x7F800000u ? N - 1 : 0u;  // +inf, NaN
+  if (b >= 0x3F800000u) return N - 1;                       // >= 1
+  const uint32_t E = b >> 23;                               // biased exponent, <= 126
+  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | (E ? 0x800000u : 0u));
+  const uint32_t sh = E ? 150u - E : 149u;                  // bhat = m 2^-sh, sh >= 24
+  return sh >= 64u ? 0u : (uint32_t)((m * N) >> sh);
+}
+
+// Decode one gene pair (Eq. aenc / Eq. benc in rank form): a = floor(ahat)
+// clamped to {0..F}; theta = min(floor(bhat (n_p + 1)), n_p - 1).
 __device__ __forceinline__ void decode_gene_pair(float ahat, float bhat, int F,
                                                  const uint32_t* __restrict__ n_unique, int* a_out,
                                                  uint32_t* theta_out) {
@@ -287,14 +305,10 @@ __device__ __forceinline__ void decode_gene_pair(float ahat, float bhat, int F,
     *theta_out = 0;
     return;
   }
-  uint32_t np = n_unique[a - 1];
-  double raw = floor(__dmul_rn((double)bhat, (double)((uint64_t)np + 1)));
-  if (raw < 0.0) raw = 0.0;
-  if (raw > (double)np) raw = (double)np;
-  uint32_t th = (uint32_t)raw;
-  if (th > np - 1) th = np - 1;
+  const uint32_t np = n_unique[a - 1];
+  const uint32_t raw = floor_times(bhat, np + 1u);  // in 0..n_p
   *a_out = a;
-  *theta_out = th;
+  *theta_out = raw > np - 1 ? np - 1 : raw;
 }
 
 }  // namespace deoct

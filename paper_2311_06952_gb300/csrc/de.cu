@@ -19,28 +19,24 @@ __device__ __forceinline__ const DEProb& prob_of(const DEArgs& a) {
   return a.probs ? a.probs[blockIdx.x] : a.single;
 }
 
-// Fitness of Section 3.2 from the class counts of individual r:
-// f = (errors + V) + alpha * splits, errors = n - sum_leaf max_k count,
-// V = #{leaf : 0 < n_leaf < n_min}, splits = #{t : a_t >= 1} (ahat_t >= 1).
-__device__ double fitness_of(const uint32_t* __restrict__ c, const float* __restrict__ genes, int B,
-                             int L, int K, int64_t n_valid, int n_min, double alpha) {
-  int64_t correct = 0;
-  uint32_t v = 0;
-  for (int l = 0; l < L; ++l) {
-    uint32_t mx = 0;
-    int64_t nl = 0;
-    for (int k = 0; k < K; ++k) {
-      uint32_t x = c[l * K + k];
-      mx = x > mx ? x : mx;
-      nl += x;
-    }
-    correct += mx;
-    if (nl > 0 && nl < n_min) v += 1;
-  }
-  uint32_t splits = 0;
-  for (int t = 0; t < B; ++t) splits += genes[t] >= 1.0f ? 1u : 0u;
-  const int64_t errors = n_valid - correct;
-  return __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(alpha, (double)splits));
+// (double)e for 0 <= e < 2^53 (exact), built with integer operations only: the
+// leading one sets the exponent, the bits below it the significand.
+__device__ __forceinline__ double exact_double(int64_t e) {
+  if (e <= 0) return 0.0;
+  const int lz = __clzll(e);
+  const uint64_t mant = ((uint64_t)e << (lz + 1)) >> 12;  // the 52 bits below the leading one
+  return __longlong_as_double((long long)(((uint64_t)(1086 - lz) << 52) | mant));
+}
+
+// Fitness order.  With alpha >= 0 every fitness is a non-negative double (not
+// -0), whose bit pattern as a signed 64-bit integer orders exactly like the
+// value, so comparisons need no FP64 arithmetic; a negative alpha compares the
+// doubles.
+__device__ __forceinline__ bool fit_le(double x, double y, bool bits) {
+  return bits ? __double_as_longlong(x) <= __double_as_longlong(y) : x <= y;
+}
+__device__ __forceinline__ bool fit_lt(double x, double y, bool bits) {
+  return bits ? __double_as_longlong(x) < __double_as_longlong(y) : x < y;
 }
 
 __device__ __forceinline__ float clamp_gene(float v, float hi) {
@@ -48,14 +44,15 @@ __device__ __forceinline__ float clamp_gene(float v, float hi) {
   return v > hi ? hi : v;
 }
 
-// block-wide argmin (lowest index among minimal values); result in *best_s
+// block-wide argmin (lowest index among minimal values); result in *best_s.
+// bits: compare in the order of fit_lt (see there)
 __device__ void block_argmin(const double* __restrict__ fit, int P, int* best_s, double* red_f,
-                             int* red_i) {
+                             int* red_i, bool bits) {
   double bf = 0.0;
   int bi = -1;
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
     double f = fit[r];
-    if (bi < 0 || f < bf) {
+    if (bi < 0 || fit_lt(f, bf, bits)) {
       bf = f;
       bi = r;
     }
@@ -64,7 +61,7 @@ __device__ void block_argmin(const double* __restrict__ fit, int P, int* best_s,
   for (int off = 16; off > 0; off >>= 1) {
     double of = __shfl_down_sync(0xFFFFFFFFu, bf, off);
     int oi = __shfl_down_sync(0xFFFFFFFFu, bi, off);
-    if (oi >= 0 && (bi < 0 || of < bf || (of == bf && oi < bi))) {
+    if (oi >= 0 && (bi < 0 || fit_lt(of, bf, bits) || (!fit_lt(bf, of, bits) && oi < bi))) {
       bf = of;
       bi = oi;
     }
@@ -82,7 +79,7 @@ __device__ void block_argmin(const double* __restrict__ fit, int P, int* best_s,
     for (int w = 1; w < nw; ++w) {
       int oi = red_i[w];
       double of = red_f[w];
-      if (oi >= 0 && (i0 < 0 || of < f0 || (of == f0 && oi < i0))) {
+      if (oi >= 0 && (i0 < 0 || fit_lt(of, f0, bits) || (!fit_lt(f0, of, bits) && oi < i0))) {
         f0 = of;
         i0 = oi;
       }
@@ -124,11 +121,13 @@ __global__ void __launch_bounds__(1024) de_init_kernel(const DEArgs a) {
   if (threadIdx.x == 0 && pb.gen) *pb.gen = 1;
 }
 
-// The fitness of individual r by its group of G lanes (G a power of two that
-// divides 32; `sub` the lane's place in the group, `gm` the group's lane mask):
-// each lane takes leaves sub, sub + G, ... and genes sub, sub + G, ..., and the
-// integer partial sums meet by shuffles, so every lane returns the value
-// fitness_of gives.
+// The fitness of Section 3.2 of individual r from its class counts,
+//   f = (errors + V) + alpha * splits, errors = n - sum_leaf max_k count,
+//   V = #{leaf : 0 < n_leaf < n_min}, splits = #{t : a_t >= 1} (ahat_t >= 1),
+// by its group of G lanes (G a power of two that divides 32; `sub` the lane's
+// place in the group, `gm` the group's lane mask): each lane takes leaves sub,
+// sub + G, ... and genes sub, sub + G, ..., and the integer partial sums meet
+// by shuffles, so every lane returns the same value.
 __device__ double group_fitness(const uint32_t* __restrict__ c, const float* __restrict__ genes,
                                 int B, int L, int K, int64_t n_valid, int n_min, double alpha,
                                 int sub, int G, uint32_t gm) {
@@ -152,8 +151,12 @@ __device__ double group_fitness(const uint32_t* __restrict__ c, const float* __r
     splits += __shfl_xor_sync(gm, splits, o);
   }
   const int64_t errors = n_valid - (int64_t)correct;
+  // alpha = 0 (the default): the fitness is the integer errors + V, and
+  // (errors + V) + 0 * splits is that integer exactly
+  if (alpha == 0.0) return exact_double(errors + (int64_t)v);
   return __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(alpha, (double)splits));
 }
+
 
 // One CTA per subproblem; each individual is worked on by a group of `lanes`
 // consecutive threads (lanes x P <= blockDim.x, lanes <= 4), which shortens the
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   const uint32_t gm = (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
   const int r0 = threadIdx.x / G, rstep = blockDim.x / G;
 
+  const bool bits = a.alpha >= 0.0;  // fitness order by bit patterns (see fit_lt)
   if (threadIdx.x == 0) g_s = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
 
   if (flags & (DE_FIRST | DE_SELECT)) {
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
         const double fr = pb.fit[r];
         __syncwarp(gm);
         if (sub == 0) pb.fit_trial[r] = f;
-        if (f <= fr) {  // Eq. selection: ties go to the trial
+        if (fit_le(f, fr, bits)) {  // Eq. selection: ties go to the trial
           float* dst = pb.pop + (int64_t)r * m;
           for (int q = sub; q < m; q += G) dst[q] = genes[q];
           if (sub == 0) pb.fit[r] = f;
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
       }
     }
     __syncthreads();
-    block_argmin(pb.fit, P, &best_s, red_f, red_i);
+    block_argmin(pb.fit, P, &best_s, red_f, red_i, bits);
     if (threadIdx.x == 0) *pb.best = best_s;
   } else {
     if (threadIdx.x == 0) best_s = *pb.best;
