@@ -300,6 +300,30 @@ DE_CASES = [
     ("w0", 2, 200, 8, 0.9, False, False, 2, 4),        # 4 threads per individual in the step
     ("rand_k3", 3, 300, 5, 0.5, True, False, 13, 6),   # 2 threads per individual
 ]
+# alpha and n_min of the fitness (Section 3.2): 0 / 1 above; a positive alpha, a negative one
+# (the step then orders fitness as doubles, not as bit patterns) and n_min > 1
+ALPHA_CASES = [(0.75, 1), (-0.25, 1), (0.0, 40), (0.5, 25)]
+
+
+@pytest.mark.parametrize("alpha,n_min", ALPHA_CASES)
+def test_de_trajectory_alpha_nmin_bit_exact(c, alpha, n_min):
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(88)
+    X = np.round(rng.random((3000, 5)), 2).astype(np.float32)
+    y = datagen.flip_labels(datagen.planted_tree_labels(X, 3, 3, rng), 3, 0.2, rng)
+    ds = gpu_dataset(c, X, y, 3, 2)
+    ranks, nu = oracle.encode(X)
+    P, G, depth = 40, 12, 3
+    ref = oracle.de_run(ranks, nu, y, 3, depth=depth, P=P, G=G, alpha=alpha, n_min=n_min, seed=3,
+                        history=True)
+    prm = deoct.make_params(depth, P, G, alpha=alpha, n_min=n_min, seed=3)
+    pop, fit, best = deoct.deoct_de_init(c, ds, prm)
+    np.testing.assert_array_equal(fit.cpu().numpy(), ref["fit_hist"][0])
+    for g in range(1, G + 1):
+        deoct.deoct_de_step(c, ds, prm, g, pop, fit, best)
+        np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), ref["pop_hist"][g].view(np.uint32))
+        np.testing.assert_array_equal(fit.cpu().numpy(), ref["fit_hist"][g])
+    assert int(best.cpu()[0]) == ref["best"]
 
 
 @pytest.mark.parametrize("case", DE_CASES, ids=[str(x[:4]) for x in DE_CASES])

@@ -134,3 +134,48 @@ def test_scratch_bound_covers_a_fresh_context(case):
     bound = deoct.fit_scratch_bound(n, F, K, prm)
     assert held <= bound, (held, bound)
     assert held >= bound // 8  # the bound is not vacuous
+
+
+def test_engine_with_warm_starts_and_dither_equals_oracle():
+    """A context attached to the engine, fitting with both warm starts of Algorithm 2 and the
+    dithered M of Section 3.3 (the level solves' seeds pass through the engine's problems),
+    gives the oracle's tree; a second context shares the engine at the same time."""
+    import threading
+
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    rng = np.random.Generator(np.random.PCG64(17))
+    sets = []
+    for n, F, K in ((6000, 6, 3), (9000, 5, 2)):
+        X = np.round(rng.random((n, F)), 3).astype(np.float32)
+        y = datagen.flip_labels(datagen.planted_tree_labels(X, 4, K, rng), K, 0.1, rng)
+        sets.append((X, y, K))
+    eng = deoct.Engine(0)
+    flags = deoct.DEOCT_BATCHED | deoct.DEOCT_CART_SEEDS | deoct.DEOCT_DE_SEEDS | deoct.DEOCT_DITHER_M
+    outs = [None, None]
+
+    def fit(i):
+        X, y, K = sets[i]
+        ctx = deoct.Context(0)
+        ctx.attach_engine(eng)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ds = deoct.encode_dataset(ctx, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), K, 0, stream=s)
+            prm = deoct.make_params(5, 16, 20, cr=0.5, seed=9 + i, horizon=3, flags=flags)
+            outs[i] = deoct.deoct_fit_moving_horizon(ctx, ds, prm, stream=s)
+        ctx.close()
+
+    threads = [threading.Thread(target=fit, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    st = eng.stats()
+    eng.close()
+    for i, (X, y, K) in enumerate(sets):
+        ranks, nu = oracle.encode(X)
+        ref = oracle.mh(ranks, nu, y, K, depth=5, horizon=3, P=16, G=20, CR=0.5, seed=9 + i, dither=True,
+                        cart_seeds=True, de_seeds=True)
+        for k in ("kind", "a", "theta", "node_fit", "leaf_class"):
+            np.testing.assert_array_equal(outs[i][k].astype(ref[k].dtype), ref[k], err_msg="set %d %s" % (i, k))
+    assert st["completed"] == st["submissions"] > 0
