@@ -85,7 +85,7 @@ def _eval_source_hash():
     import hashlib
     csrc = os.path.join(ROOT, "paper_2311_06952_gb300", "csrc")
     ev = open(os.path.join(csrc, "eval.cu")).read()
-    a = ev.index("__global__ void __launch_bounds__(512, 2) eval_kernel(")
+    a = ev.index(" eval_kernel(const __grid_constant__")
     a = ev.rindex("template", 0, a)
     b = ev.index("int launch_t(", a)
     h = hashlib.sha256(_strip_comments(ev[a:b]).encode())

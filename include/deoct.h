@@ -123,7 +123,8 @@ DEOCT_API int deoct_reset_stats(deoct_ctx* ctx);
 /* Override the evaluator's launch shape (0 keeps the library's choice):
  *  S      samples per shared-memory tile (multiple of 128, 128..8192)
  *  TG     trees per job (tree group), 1..4096
- *  warps  warps per CTA, 1..16
+ *  warps  warps per CTA, 1..32 (the streaming kernel, which evaluates groups of
+ *         fewer than 16 trees, takes at most 16)
  *  grid   persistent CTAs (each walks an equal contiguous range of tiles)
  * Results do not depend on the shape; only speed does.  Invalid values are
  * DEOCT_ERR_INVALID; a shape whose tile does not fit in shared memory fails at

@@ -445,7 +445,7 @@ int deoct_set_eval_config(deoct_ctx* ctx, int32_t S, int32_t TG, int32_t warps, 
   if (S != 0 && (S < 128 || S > 8192 || S % 128 != 0))
     return set_error(DEOCT_ERR_INVALID, "S = %d: want a multiple of 128 in 128..8192", S);
   if (TG < 0 || TG > kMaxPop) return set_error(DEOCT_ERR_INVALID, "TG = %d out of range", TG);
-  if (warps < 0 || warps > 16) return set_error(DEOCT_ERR_INVALID, "warps = %d out of range", warps);
+  if (warps < 0 || warps > 32) return set_error(DEOCT_ERR_INVALID, "warps = %d out of range", warps);
   if (grid < 0) return set_error(DEOCT_ERR_INVALID, "grid < 0");
   ctx->force_S = S;
   ctx->force_TG = TG;

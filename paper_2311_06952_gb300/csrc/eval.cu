@@ -19,7 +19,7 @@ using namespace evk;
 namespace {
 
 template <int W, int D, int MODE, int Q>
-__global__ void __launch_bounds__(512, 2) eval_kernel(const __grid_constant__ EvalArgs a) {
+__global__ void __launch_bounds__(1024, 1) eval_kernel(const __grid_constant__ EvalArgs a) {
   constexpr int B = (1 << D) - 1;
   constexpr int L = 1 << D;
   typedef typename RankT<W>::T RT;
@@ -339,6 +339,16 @@ static size_t eval_smem(int mode, int W, int D, int S, int TG, int F, int K, int
   return smem_layout(mode, W, D, S, TG, F, K, warps, lab_stage).total;
 }
 
+int eval_ctas_per_sm(const deoct_ctx* ctx, int W, int D, int F, int K, const EvalConfig& c) {
+  const int mode = eval_mode(D, K);
+  if (use_stream(mode, W, c.TG, c.stream)) return 0;
+  const size_t smem = eval_smem(mode, W, D, c.S, c.TG, F, K, c.warps);
+  if (smem + 1024 > (size_t)ctx->max_smem_optin) return 0;
+  const int by_smem = (int)((size_t)ctx->smem_per_sm / (smem + 1024));
+  const int by_regs = 32 / std::max(1, c.warps);  // at most 64 registers a thread
+  return std::min(by_smem, by_regs);
+}
+
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob) {
   EvalConfig c;
@@ -537,6 +547,7 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
   if (!streaming && (W == 2 || cfg.S <= 256)) encode_rank_map(plan, cfg.S, W, &a);
   EvalConfig scfg = cfg;  // the streaming kernel has a producer warp and >= 1 routing warp
   if (scfg.warps < 2) scfg.warps = 2;
+  if (scfg.warps > 16) scfg.warps = 16;
   int rc = streaming ? launch_stream(ctx, W, D, Q, a, scfg, smem, stream)
            : (W == 2) ? dispatch_depth<2>(ctx, D, mode, Q, a, cfg, smem, stream)
                       : dispatch_depth<4>(ctx, D, mode, Q, a, cfg, smem, stream);

@@ -70,6 +70,9 @@ struct EvalPlan {
 
 int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalConfig& cfg,
                 cudaStream_t stream);
+// CTAs of a re-laid-kernel shape resident on one SM (shared memory and registers;
+// 0 when the shape does not fit or runs on the streaming kernel).
+int eval_ctas_per_sm(const deoct_ctx* ctx, int W, int D, int F, int K, const EvalConfig& c);
 // Choose S / TG / warps for a workload shape (heuristic, tuned by measurement).
 EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P, int64_t n,
                               int nprob);

@@ -630,6 +630,40 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
         for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG);
         if (!dup) cands.push_back(x);
       }
+    if (W == 4 && nsum >= 100000) {
+      // large uint32 levels: the last wave of tiles leaves CTAs idle (up to 10%
+      // of a launch at n = 1e6), so tile sizes between the powers of two join,
+      // with 16 warps (one or two CTAs per SM) and 32 (one CTA): for each warp
+      // count the two of least modelled makespan -- waves of tiles over the
+      // resident CTAs, a wave costing its CTAs per SM x (S + 200) -- are timed
+      for (int warps : {16, 32}) {
+        std::vector<std::pair<double, EvalConfig>> model;
+        for (int S = 256; S <= 2048; S += 128) {
+          EvalConfig x = cfg;
+          x.S = S;
+          x.TG = std::min(cfg.TG, P);
+          x.warps = warps;
+          const int per_sm = eval_ctas_per_sm(ctx, W, Dt, F, K, x);
+          if (per_sm < 1) continue;
+          int64_t tiles = 0;
+          for (int m = 0; m < M; ++m) tiles += (c.counts[m] + S - 1) / S;
+          tiles *= (P + x.TG - 1) / x.TG;
+          const int64_t slots = (int64_t)per_sm * ctx->num_sms;
+          const double waves = (double)((tiles + slots - 1) / slots);
+          model.push_back({waves * per_sm * (S + 200.0), x});
+        }
+        std::sort(model.begin(), model.end(),
+                  [](const std::pair<double, EvalConfig>& u, const std::pair<double, EvalConfig>& v) {
+                    return u.first < v.first;
+                  });
+        for (size_t i = 0; i < model.size() && i < 2; ++i) {
+          const EvalConfig& x = model[i].second;
+          bool dup = false;
+          for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG && o.warps == x.warps);
+          if (!dup) cands.push_back(x);
+        }
+      }
+    }
 
     cudaEvent_t e0, e1;
     DEOCT_CUDA_TRY(cudaEventCreate(&e0));

@@ -154,9 +154,10 @@ def test_eval_bit_exact(c, case):
 
 
 @pytest.mark.parametrize("shape", [(128, 3, 1, 1), (256, 16, 4, 3), (512, 64, 8, 7), (2048, 256, 16, 5),
-                                   (8192, 1, 2, 2)])
+                                   (8192, 1, 2, 2), (1152, 70, 32, 0), (640, 32, 32, 9), (1408, 16, 24, 0)])
 def test_eval_launch_shapes_bit_exact(c, shape):
-    """Persistent CTAs walking many tiles and several tree groups give the same counts."""
+    """Persistent CTAs walking many tiles and several tree groups give the same counts, with
+    tiles that are not powers of two and CTAs of up to 32 warps."""
     from paper_2311_06952_gb300 import deoct
     S, TG, warps, grid = shape
     rng = _rng(200 + S)
@@ -181,7 +182,7 @@ def test_eval_launch_shapes_bit_exact(c, shape):
 
 
 @pytest.mark.parametrize("shape", [(0, 0, 0, 0), (256, 128, 16, 0), (512, 64, 16, 7), (1024, 16, 6, 3),
-                                   (128, 200, 16, 2)])
+                                   (128, 200, 16, 2), (768, 32, 32, 0)])
 @pytest.mark.parametrize("depth,K", [(3, 4), (4, 2), (2, 30), (5, 3)])
 def test_eval_streaming_kernel_large_groups_bit_exact(c, shape, depth, K):
     """The streaming kernel forced for groups of 16+ trees (shared class masks, trees split over
@@ -212,7 +213,8 @@ def test_eval_streaming_kernel_large_groups_bit_exact(c, shape, depth, K):
         c.set_eval_config(0, 0, 0, 0)
 
 
-@pytest.mark.parametrize("shape", [(0, 0, 0, 0), (128, 2, 16, 3), (1024, 8, 16, 5), (512, 1, 4, 1)])
+@pytest.mark.parametrize("shape", [(0, 0, 0, 0), (128, 2, 16, 3), (1024, 8, 16, 5), (512, 1, 4, 1),
+                                   (1152, 8, 32, 0)])
 @pytest.mark.parametrize("depth,K", [(7, 3), (4, 29)])
 def test_eval_shared_atomic_mode_shapes_bit_exact(c, shape, depth, K):
     """Many bins (2^D K > 128): warps split each tree's chunks into shared job counts."""
