@@ -45,12 +45,12 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
 # headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
 # left out.
-EVAL_TRAFFIC = {"source_sha256_16": "2a806568313e390a", "bytes": 352_957_440 + 3_821_312,
+EVAL_TRAFFIC = {"source_sha256_16": "b7baa8651f100bce", "bytes": 352_502_016 + 3_729_408,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
                 "ncu": {"inst_per_cycle": 3.336, "issue_frac": 0.8348, "alu_pipe_frac": 0.7720,
-                        "shared_pipe_frac": 2773946762 / 152 / (10.874976e-3 * 2.07e9),
-                        "inst_per_chunk": 35.46, "dram_gbs": (352_957_440 + 3_821_312) / 10.874976e-3 / 1e9,
-                        "dram_frac_of_peak": (352_957_440 + 3_821_312) / 10.874976e-3 / 1e9 / 6777.3}}
+                        "shared_pipe_frac": 2773945017 / 152 / (10.864352e-3 * 2.07e9),
+                        "inst_per_chunk": 35.46, "dram_gbs": (352_502_016 + 3_729_408) / 10.864352e-3 / 1e9,
+                        "dram_frac_of_peak": (352_502_016 + 3_729_408) / 10.864352e-3 / 1e9 / 6777.3}}
 
 
 def _strip_comments(src):
