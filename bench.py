@@ -45,12 +45,12 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
 # headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
 # left out.
-EVAL_TRAFFIC = {"source_sha256_16": "b7baa8651f100bce", "bytes": 352_502_016 + 3_729_408,
+EVAL_TRAFFIC = {"source_sha256_16": "64ebf25e87bb9a38", "bytes": 210_481_920 + 3_612_416,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
-                "ncu": {"inst_per_cycle": 3.336, "issue_frac": 0.8348, "alu_pipe_frac": 0.7720,
-                        "shared_pipe_frac": 2773945017 / 152 / (10.864352e-3 * 2.07e9),
-                        "inst_per_chunk": 35.46, "dram_gbs": (352_502_016 + 3_729_408) / 10.864352e-3 / 1e9,
-                        "dram_frac_of_peak": (352_502_016 + 3_729_408) / 10.864352e-3 / 1e9 / 6777.3}}
+                "ncu": {"inst_per_cycle": 3.4625, "issue_frac": 0.8656, "alu_pipe_frac": 0.8133,
+                        "shared_pipe_frac": 2742438088 / 152 / (10.233984e-3 * 2.07e9),
+                        "inst_per_chunk": 34.23, "dram_gbs": (210_481_920 + 3_612_416) / 10.233984e-3 / 1e9,
+                        "dram_frac_of_peak": (210_481_920 + 3_612_416) / 10.233984e-3 / 1e9 / 6777.3}}
 
 
 def _strip_comments(src):
@@ -78,10 +78,11 @@ def _strip_comments(src):
 
 
 def _eval_source_hash():
-    """Key of the evaluator kernel's code: the `eval_kernel` template of csrc/eval.cu, the
-    kernel header csrc/eval_kernel.cuh and the device helpers of csrc/common.cuh (from its
-    "device helpers" section on: the host-side context and error code above it are not the
-    kernel's), comments and whitespace left out."""
+    """Key of the evaluator kernel's code and launch shape: the `eval_kernel` template and the
+    shape chooser `eval_choose_config` of csrc/eval.cu, the kernel header csrc/eval_kernel.cuh
+    and the device helpers of csrc/common.cuh (from its "device helpers" section on: the
+    host-side context and error code above it are not the kernel's), comments and whitespace
+    left out."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2311_06952_gb300", "csrc")
     ev = open(os.path.join(csrc, "eval.cu")).read()
@@ -89,6 +90,10 @@ def _eval_source_hash():
     a = ev.rindex("template", 0, a)
     b = ev.index("int launch_t(", a)
     h = hashlib.sha256(_strip_comments(ev[a:b]).encode())
+    # the launch shape the workload gets comes from the chooser
+    a = ev.index("EvalConfig eval_choose_config(")
+    b = ev.index("\n}\n", a)
+    h.update(_strip_comments(ev[a:b]).encode())
     with open(os.path.join(csrc, "eval_kernel.cuh")) as fh:
         h.update(_strip_comments(fh.read()).encode())
     with open(os.path.join(csrc, "common.cuh")) as fh:

@@ -401,6 +401,28 @@ EvalConfig eval_choose_config(deoct_ctx* ctx, int W, int D, int F, int K, int P,
             c.TG = tg;
           }
         }
+      // One CTA of 32 warps per SM (a CTA twice as wide, so twice the trees and
+      // samples per tile for the same staging and set-up): its work items cost
+      // S TG evaluations plus about 25000 + 170 c, at 2.13 times the rate of a
+      // 16-warp CTA, fitted to shape sweeps on GB300 (n = 1e7, uint16, depth 4:
+      // 1024 x 256 with 16 warps 10.95 ms; 32 warps 10.88 ms at 1024 x 256, 10.43
+      // at 2048 x 256, 10.29 at 2048 x 512; depth 3: 8.77 vs 7.80 ms; depth 5:
+      // 11.68 vs 10.51 ms; identical counts)
+      for (int S : {3072, 2048, 1536, 1024, 512})
+        for (int TG : {512, 256, 128, 64, 32}) {
+          const int tg = std::min(TG, P);
+          if (tg < 16 || eval_smem(mode, W, D, S, tg, F, K, 32) > (size_t)limit) continue;
+          const int64_t items = work(S, tg);
+          const double waves = (double)((items + ctx->num_sms - 1) / ctx->num_sms);
+          const int copies = (W == 2) ? std::max(1, S / 256) : F;
+          const double cost = waves * ((double)S * tg + 25000.0 + 170.0 * copies) / 2.13;
+          if (best < 0 || cost < best) {
+            best = cost;
+            c.S = S;
+            c.TG = tg;
+            c.warps = 32;
+          }
+        }
       if (best < 0) {  // nothing keeps two CTAs per SM: the largest shape that fits
         c.S = 2048;
         c.TG = std::min(P, 256);

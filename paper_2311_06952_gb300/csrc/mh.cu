@@ -617,7 +617,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   const bool forced = ctx->force_S || ctx->force_TG || ctx->force_warps || ctx->force_grid || ctx->force_stream;
   if (!have && !forced) {
     // candidates around the heuristic; each runs the real evaluation of S^1
-    std::vector<EvalConfig> cands;
+    std::vector<EvalConfig> cands{cfg};  // the heuristic's own shape first
     for (int S : {256, 512, 1024, 2048})
       for (int TG : {cfg.TG, std::max(1, cfg.TG / 2), P}) {
         EvalConfig x = cfg;
@@ -627,12 +627,12 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
         // pairs over warps); shared atomics: warps split a tree's chunks
         x.warps = 16;
         bool dup = false;
-        for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG);
+        for (const EvalConfig& o : cands) dup = dup || (o.S == x.S && o.TG == x.TG && o.warps == x.warps);
         if (!dup) cands.push_back(x);
       }
-    if (W == 4 && nsum >= 100000) {
-      // large uint32 levels: the last wave of tiles leaves CTAs idle (up to 10%
-      // of a launch at n = 1e6), so tile sizes between the powers of two join,
+    if (nsum >= 100000) {
+      // large levels: the last wave of tiles leaves CTAs idle (up to 10% of a
+      // uint32 launch at n = 1e6), so tile sizes between the powers of two join,
       // with 16 warps (one or two CTAs per SM) and 32 (one CTA): for each warp
       // count the two of least modelled makespan -- waves of tiles over the
       // resident CTAs, a wave costing its CTAs per SM x (S + 200) -- are timed

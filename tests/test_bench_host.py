@@ -71,3 +71,16 @@ def test_source_key_covers_the_device_helpers_only(tmp_path, monkeypatch):
     common.write_text(text.replace("return (uint32_t)(((uint64_t)x * (uint64_t)m) >> 32);",
                                    "return (uint32_t)(((uint64_t)x * (uint64_t)m) >> 31);", 1))
     assert bench._eval_source_hash() != base
+
+
+def test_source_key_covers_the_shape_chooser(tmp_path, monkeypatch):
+    """The stored counters belong to one launch shape: a change of the chooser's constants
+    changes the key."""
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", root)
+    base = bench._eval_source_hash()
+    ev = csrc / "eval.cu"
+    text = ev.read_text()
+    assert "25000.0 + 170.0 * copies" in text
+    ev.write_text(text.replace("25000.0 + 170.0 * copies", "26000.0 + 170.0 * copies", 1))
+    assert bench._eval_source_hash() != base
