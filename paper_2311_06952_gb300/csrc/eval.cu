@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(1024, 1) eval_kernel(const __grid_constant__ E
     // ---- labels: class masks (ballot) or per-sample labels (atomic) -------
     const int lab_done = tma_label_bytes(P, ns, a.lab_stage);
     if (MODE == 0) {
-      class_masks<Q, PairGeom<W, false>::kShared>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane,
+      class_masks<D, Q, PairGeom<W, false>::kShared>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane,
                                                   warp, nw, aux32);
     } else {
       for (int j = threadIdx.x; j < 2 * npair * 32; j += blockDim.x)

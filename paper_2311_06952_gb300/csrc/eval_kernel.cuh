@@ -289,20 +289,32 @@ __device__ __forceinline__ void route_levels(uint32_t jb, uint32_t row0, uint32_
   }
 }
 
-// Whether the bins of a job share classes across a lane: with 2^D K = 32 Q
-// bins and K dividing 32, bin lane + 32 q has class lane % K for every q and
-// leaf lane / K + q 32 / K, so its leaves differ only in the top log2 Q levels.
+// The class-major map of bins to lanes, for Q = 2 and 4 bins per lane (depth
+// at least log2 Q): with s = LK / Q = 2^(D - log2 Q) K, lane l < s owns bins
+// q s + l (q < Q), all of class l % K and of leaf q 2^(D - log2 Q) + l / K, so
+// they differ only in the top log2 Q levels and share the class mask and the
+// levels below; lanes s..31 are idle.  Otherwise (Q = 1, 3) lane l owns bins
+// l + 32 q, each with its own class.
 template <int D, int Q>
-__device__ __forceinline__ bool shared_class(int LK) {
-  const int K = LK >> D;
-  return (Q == 2 || Q == 4) && LK == 32 * Q && K > 0 && 32 % K == 0;
+__host__ __device__ constexpr bool class_major() {
+  return (Q == 2 && D >= 1) || (Q == 4 && D >= 2);
+}
+// Bin of slot q of `lane` (-1: the slot is unused).
+template <int D, int Q>
+__device__ __forceinline__ int bin_of(int lane, int q, int LK) {
+  if constexpr (class_major<D, Q>()) {
+    const int s = LK / Q;
+    return lane < s ? q * s + lane : -1;
+  } else {
+    const int b = lane + 32 * q;
+    return b < LK ? b : -1;
+  }
 }
 
-// Route 64 samples (the two chunks of pair p) of one tree and add the bin
-// counts owned by this lane: bin b = leaf*K + k is owned by lane b % 32, and
-// its count grows by popc(Y_k & AND_d (B_d or ~B_d)).  SC (a job for which
-// shared_class holds): the class mask and the levels below the top log2 Q are
-// ANDed once for all bins of the lane.
+// Route 64 samples (the two chunks of pair p) of one tree and add the counts
+// of the bins this lane owns (bin_of): the count of bin b = leaf K + k grows by
+// popc(Y_k & AND_d (B_d or ~B_d)).  SC (the class-major map): the class mask
+// and the levels below the top log2 Q are ANDed once for all bins of the lane.
 template <int W, int D, int Q, bool NAT, bool R32, bool SC = false>
 __device__ __forceinline__ void route_pair(uint32_t jb, uint32_t row0, uint32_t th0, uint32_t row2,
                                            uint32_t th2, uint32_t row3, uint32_t th3, uint32_t tnb32,
@@ -372,7 +384,7 @@ __device__ __forceinline__ void route_group(int nt, int npair, uint32_t jb0, con
                                             int lane, int warp, int nw) {
   constexpr int B = (1 << D) - 1;
   typedef PairGeom<W, NAT> G;
-  const bool sc = shared_class<D, Q>(LK);
+  typedef std::integral_constant<bool, class_major<D, Q>()> SCM;
   auto route_tree = [&](int i, int sl, int step) {
     const uint32_t tnb = nodes_sa + (uint32_t)(i * B - 1) * 8u;  // node t at tnb + 8t
     const uint2 n1 = nodes_s[i * B];
@@ -408,19 +420,10 @@ __device__ __forceinline__ void route_group(int nt, int npair, uint32_t jb0, con
           for (; pp < npair; pp += step) one(pp, r32, scc);
         }
       };
-      auto walk_sc = [&](auto r32) {
-        if constexpr (Q == 2 || Q == 4) {
-          if (sc) {
-            walk(r32, std::true_type{});
-            return;
-          }
-        }
-        walk(r32, std::false_type{});
-      };
       if (n1.y <= 0xFFFFu)
-        walk_sc(std::true_type{});
+        walk(std::true_type{}, SCM{});
       else
-        walk_sc(std::false_type{});
+        walk(std::false_type{}, SCM{});
     } else {
       auto walk = [&](auto scc) {
         for (int pp = sl; pp < npair; pp += step) {
@@ -432,19 +435,12 @@ __device__ __forceinline__ void route_group(int nt, int npair, uint32_t jb0, con
                                                                 ymA, ymB, cst, cnt);
         }
       };
-      if constexpr (Q == 2 || Q == 4) {
-        if (sc)
-          walk(std::true_type{});
-        else
-          walk(std::false_type{});
-      } else {
-        walk(std::false_type{});
-      }
+      walk(SCM{});
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int b = lane + 32 * q;
-      if (b < LK) atomicAdd(&cnt_s[i * LK + b], cnt[q]);
+      const int b = bin_of<D, Q>(lane, q, LK);
+      if (b >= 0) atomicAdd(&cnt_s[i * LK + b], cnt[q]);
     }
   };
   if (nt >= nw) {
@@ -492,8 +488,8 @@ __device__ __forceinline__ void setup_job(const JobView& jv, uint2* nodes_s, uin
   if (BALLOT) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int b = lane + 32 * q;
-      int leaf = (b < LK) ? b / K : 0;
+      const int b = bin_of<D, Q>(lane, q, LK);
+      const int leaf = b >= 0 ? b / K : 0;
 #pragma unroll
       for (int d = 0; d < D; ++d) cst[q][d] = ((leaf >> (D - 1 - d)) & 1) ? 0u : 0xFFFFFFFFu;
     }
@@ -571,15 +567,15 @@ __device__ __forceinline__ uint32_t tile_label(const EvalProb& P, const uint8_t*
 // EVENODD: chunk 2p holds the even and chunk 2p + 1 the odd samples of the
 // 64-sample block p (lane l: samples 64p + 2l and 64p + 2l + 1), else chunk c
 // holds samples 32c .. 32c + 31.
-template <int Q, bool PAIRED, bool EVENODD = false>
+template <int D, int Q, bool PAIRED, bool EVENODD = false>
 __device__ __forceinline__ void class_masks(const EvalProb& P, const uint8_t* lab_land, int lab_done,
                                             int64_t s0, int ns, int npair, int K, int LK, int lane,
                                             int warp, int nw, uint32_t* aux32) {
   int kq[Q];  // class of each bin this lane owns (-1: none)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int b = lane + 32 * q;
-    kq[q] = (b < LK) ? b % K : -1;
+    const int b = bin_of<D, Q>(lane, q, LK);
+    kq[q] = b >= 0 ? b % K : -1;
   }
   for (int c = warp; c < 2 * npair; c += nw) {
     const int j = EVENODD ? 64 * (c >> 1) + 2 * lane + (c & 1) : c * 32 + lane;

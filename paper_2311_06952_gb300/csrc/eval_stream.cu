@@ -52,7 +52,7 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
   constexpr bool EO = (W == 2);  // even/odd chunks on words shared by a pair
   typedef PairGeom<W, !EO> G;
   if (warp >= npair) return;
-  const bool sc = shared_class<D, Q>(LK);
+  typedef std::integral_constant<bool, class_major<D, Q>()> SCM;
   auto put = [&](int c, int q, uint32_t m) {
     if (EO)
       aux32[((c >> 1) * Q + q) * 64 + lane * 2 + (c & 1)] = m;
@@ -61,8 +61,8 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
   };
   if (K == 2 && lab_done >= 64 * npair) {
     // two classes, every label of the tile landed: all bins of a lane have
-    // class lane % 2 (bin lane + 32 q), so one pair of ballots per chunk
-    // serves them
+    // class lane % 2 (bins lane + 32 q, or q s + lane with s even), so one
+    // pair of ballots per chunk serves them
     const bool odd = lane & 1;
     for (int pp = warp; pp < npair; pp += ncw) {
       uint32_t ya, yb;
@@ -131,27 +131,18 @@ __device__ __forceinline__ void route_share(const EvalProb& P, int nt, int npair
             ymA, ymB, cst, cnt);
       }
     };
-    auto walk_sc = [&](auto r32) {
-      if constexpr (Q == 2 || Q == 4) {
-        if (sc) {
-          walk(r32, std::true_type{});
-          return;
-        }
-      }
-      walk(r32, std::false_type{});
-    };
     if constexpr (EO) {
       if (n1.y <= 0xFFFFu)
-        walk_sc(std::true_type{});
+        walk(std::true_type{}, SCM{});
       else
-        walk_sc(std::false_type{});
+        walk(std::false_type{}, SCM{});
     } else {
-      walk_sc(std::false_type{});
+      walk(std::false_type{}, SCM{});
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int b = lane + 32 * q;
-      if (b < LK) atomicAdd(&cnt_s[i * LK + b], cnt[q]);
+      const int b = bin_of<D, Q>(lane, q, LK);
+      if (b >= 0) atomicAdd(&cnt_s[i * LK + b], cnt[q]);
     }
   }
 }
@@ -263,8 +254,8 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
         setup_job<D, Q, true>(jv, nodes_s, cnt_s, stage0_sa, S, W, a.status, lane, nct, cst, &K, &LK);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int b = lane + 32 * q;
-          kq[q] = (b < LK) ? b % K : -1;
+          const int b = bin_of<D, Q>(lane, q, LK);
+          kq[q] = b >= 0 ? b % K : -1;
         }
         bar_sync_n(nct);  // node table and zeroed counts visible to every warp
       }
@@ -321,7 +312,7 @@ __global__ void __launch_bounds__(512, 2) eval_stream_kernel(const __grid_consta
         // larger groups: the tile's class masks once, shared by every warp
         // (uint16: even/odd chunks on shared words, as in route_share)
         if (!dead)
-          class_masks<Q, W == 2, W == 2>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp,
+          class_masks<D, Q, W == 2, W == 2>(P, lab_land, lab_done, s0, ns, npair, K, LK, lane, warp,
                                          ncw, aux32);
         bar_sync_n(nct);
         if (!dead)
