@@ -234,7 +234,9 @@ int dispatch_mode(deoct_ctx* ctx, int mode, int Q, const EvalArgs& args, const E
   switch (Q) {
     case 1: return launch_t<W, D, 0, 1>(ctx, args, cfg, smem, s);
     case 2: return launch_t<W, D, 0, 2>(ctx, args, cfg, smem, s);
-    case 3: return launch_t<W, D, 0, 3>(ctx, args, cfg, smem, s);
+    case 3:  // three slots only at depth 1 (bins_per_lane)
+      if constexpr (D == 1) return launch_t<W, D, 0, 3>(ctx, args, cfg, smem, s);
+      return launch_t<W, D, 0, 4>(ctx, args, cfg, smem, s);
     default: return launch_t<W, D, 0, 4>(ctx, args, cfg, smem, s);
   }
 }
@@ -562,7 +564,7 @@ int eval_launch(deoct_ctx* ctx, int W, int D, const EvalPlan& plan, const EvalCo
     DEOCT_CUDA_TRY(cudaEventCreate(&e1));
     DEOCT_CUDA_TRY(cudaEventRecord(e0, stream));
   }
-  const int Q = ((1 << D) * plan.Kmax + 31) / 32;
+  const int Q = bins_per_lane(D, (1 << D) * plan.Kmax);
   // re-laid kernel: a tile arrives as 2-D tensor boxes (uint16: S / BX boxes;
   // uint32: one box, tiles of at most 256 samples)
   a.tmap_box = 0;

@@ -111,6 +111,14 @@ __device__ __forceinline__ void advance_job(const EvalArgs& a, int64_t gt_next, 
 
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
+// Bin slots per lane in ballot mode, ceil(2^D K / 32), three rounded up to four
+// from depth 2 on: four slots take the class-major map (one class and the lower
+// levels shared by a lane's bins), three would keep one class per bin.
+__host__ __device__ __forceinline__ int bins_per_lane(int D, int LK) {
+  const int q = (LK + 31) / 32;
+  return (q == 3 && D >= 2) ? 4 : q;
+}
+
 // Shared-memory layout of the re-laid kernel (host sizing and kernel agree):
 //   tile    [F][S] ranks in the compute layout (see tile_offset)
 //   stage   [F][S] TMA landing zone (uint16 only; the uint32 path lands in `tile`)
@@ -134,7 +142,7 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(int mode, int W, int 
   s.nodes = s.stage + (W == 2 ? rows : 0);
   s.aux = s.nodes + align128((size_t)TG * B * 8);
   if (mode == 0) {
-    const int Q = (LK + 31) / 32;
+    const int Q = bins_per_lane(D, LK);
     s.lab = s.aux + align128((size_t)S * Q * 4);
   } else {
     s.lab = s.aux + align128((size_t)S);
@@ -157,7 +165,7 @@ __host__ __device__ __forceinline__ StreamLayout stream_layout(int W, int D, int
                                                                int lab_stage) {
   const int B = (1 << D) - 1, L = 1 << D;
   const int LK = L * Kmax;
-  const int Q = (LK + 31) / 32;
+  const int Q = bins_per_lane(D, LK);
   StreamLayout s;
   s.rbytes = align128((size_t)Fmax * S * W);
   s.sbytes = s.rbytes + (lab_stage ? align128((size_t)S) : 0);

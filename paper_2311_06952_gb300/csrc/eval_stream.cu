@@ -339,7 +339,10 @@ int dispatch_q(deoct_ctx* ctx, int Q, const EvalArgs& args, const EvalConfig& cf
   switch (Q) {
     case 1: return launch_kernel(ctx, eval_stream_kernel<W, D, 1>, args, cfg, smem, s, "eval_stream_kernel");
     case 2: return launch_kernel(ctx, eval_stream_kernel<W, D, 2>, args, cfg, smem, s, "eval_stream_kernel");
-    case 3: return launch_kernel(ctx, eval_stream_kernel<W, D, 3>, args, cfg, smem, s, "eval_stream_kernel");
+    case 3:  // three slots only at depth 1 (bins_per_lane)
+      if constexpr (D == 1)
+        return launch_kernel(ctx, eval_stream_kernel<W, D, 3>, args, cfg, smem, s, "eval_stream_kernel");
+      return launch_kernel(ctx, eval_stream_kernel<W, D, 4>, args, cfg, smem, s, "eval_stream_kernel");
     default: return launch_kernel(ctx, eval_stream_kernel<W, D, 4>, args, cfg, smem, s, "eval_stream_kernel");
   }
 }
