@@ -634,3 +634,56 @@ def test_deoct_workload0_matches_golden_fixture(c):
     assert [int(x) for x in th] == gold["best_tree_theta"]
     assert fit == gold["best_fitness_per_generation"][-1]
     assert hashlib.sha256(pop.cpu().numpy().tobytes()).hexdigest() == gold["final_population_sha256"]
+
+
+def _fuzz_case(seed):
+    """A random evaluation shape: depth, classes (mostly ballot counting, 2^D K <= 128,
+    sometimes shared atomics), population, rank width, data size and ties, an optional
+    subset, and a forced launch shape kept within shared memory (or the automatic one)."""
+    rng = _rng(9000 + seed)
+    depth = int(rng.integers(1, 9))
+    if depth <= 6 and rng.random() < 0.7:
+        K = int(rng.integers(2, max(2, 128 >> depth) + 1))
+    else:
+        K = int(rng.integers(2, max(2, min(64, 4096 >> depth)) + 1))
+    P = int(rng.choice([1, 2, 3, 5, 8, 13, 16, 17, 40, 64, 100, 129, 256, 300]))
+    W = int(rng.choice([2, 4]))
+    n = int(rng.integers(1, 30000))
+    F = int(rng.integers(1, 13))
+    levels = int(rng.choice([3, 50, 1000, 60000]))
+    X = (np.floor(rng.random((n, F)) * levels) / levels).astype(np.float32)
+    y = rng.integers(0, K, n).astype(np.uint8)
+    subset = bool(rng.integers(0, 2)) and n > 1
+    shape = (0, 0, 0, 0)
+    if rng.integers(0, 2):
+        B, LK = (1 << depth) - 1, (1 << depth) * K
+        tg_max = max(1, min(8192 // LK, 4096 // B))
+        tg = int(rng.choice([0, 16, 32, 64, 256]))
+        S = int(rng.choice([128, 256, 384, 640, 1024]))
+        shape = (S, min(tg, tg_max), int(rng.choice([0, 4, 16, 32])), int(rng.choice([0, 3, 40])))
+    return rng, depth, K, P, W, n, F, X, y, subset, shape
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_eval_random_shapes_bit_exact(c, seed):
+    """Forty seeded random shapes through the one-launch evaluator (both kernels, both count
+    modes, every bin map, forced and automatic launch shapes): counts and errors equal the
+    oracle's."""
+    from paper_2311_06952_gb300 import deoct
+    rng, depth, K, P, W, n, F, X, y, subset, shape = _fuzz_case(seed)
+    ranks, nu = oracle.encode(X)
+    if W == 2 and int(nu.max()) > 65536:
+        W = 4
+    a, th = datagen.random_population(nu, P, depth, rng, allow_nosplit=True)
+    idx = np.sort(rng.choice(n, max(1, n // 2), replace=False)).astype(np.int32) if subset else None
+    ref = oracle.eval_counts(ranks, y, K, a, th, depth, idx=idx)
+    _, ref_err, _, _ = oracle.fitness(ref, a, n if idx is None else len(idx))
+    try:
+        c.set_eval_config(*shape)
+        ds = gpu_dataset(c, X, y, K, W)
+        counts, errors = deoct.deoct_eval_population(c, ds, to_dev(a.astype(np.uint16)), to_dev(th), depth,
+                                                     sample_idx=None if idx is None else to_dev(idx))
+    finally:
+        c.set_eval_config(0, 0, 0, 0)
+    np.testing.assert_array_equal(u32(counts), ref, err_msg=str((depth, K, P, W, n, F, subset, shape)))
+    np.testing.assert_array_equal(u32(errors), ref_err)
