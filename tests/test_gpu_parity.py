@@ -328,6 +328,48 @@ def test_de_trajectory_alpha_nmin_bit_exact(c, alpha, n_min):
     assert int(best.cpu()[0]) == ref["best"]
 
 
+def test_de_resumes_from_saved_state_bit_exact(c):
+    """Checkpoint and resume of a DEOCT run through the C ABI: the state is the population,
+    its fitness, the best index and the generation number (the draws are Philox counters
+    keyed by seed, node and generation), so a run stopped after generation 5, saved to the
+    host, and continued from generation 6 by a new context on a new dataset handle ends with
+    the same population, fitness and best as the run that never stopped, and as the oracle."""
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    rng = _rng(91)
+    X = np.round(rng.random((4000, 6)), 2).astype(np.float32)
+    y = datagen.flip_labels(datagen.planted_tree_labels(X, 3, 4, rng), 4, 0.1, rng)
+    P, G, depth, K = 48, 12, 3, 4
+    prm = deoct.make_params(depth, P, G, cr=0.7, seed=11, flags=deoct.DEOCT_DITHER_M)
+    c1 = deoct.Context(0)
+    ds1 = gpu_dataset(c1, X, y, K, 2)
+    pop, fit, best = deoct.deoct_de_init(c1, ds1, prm, stream_id=5)
+    for g in range(1, G + 1):
+        deoct.deoct_de_step(c1, ds1, prm, g, pop, fit, best, stream_id=5)
+    straight = (pop.cpu().numpy().copy(), fit.cpu().numpy().copy(), int(best.cpu()[0]))
+    pop, fit, best = deoct.deoct_de_init(c1, ds1, prm, stream_id=5)
+    for g in range(1, 6):
+        deoct.deoct_de_step(c1, ds1, prm, g, pop, fit, best, stream_id=5)
+    saved = (pop.cpu().numpy().copy(), fit.cpu().numpy().copy(), best.cpu().numpy().copy())
+    c1.close()
+    c2 = deoct.Context(0)
+    ds2 = gpu_dataset(c2, X, y, K, 2)
+    pop = torch.from_numpy(saved[0]).cuda()
+    fit = torch.from_numpy(saved[1]).cuda()
+    best = torch.from_numpy(saved[2]).cuda()
+    for g in range(6, G + 1):
+        deoct.deoct_de_step(c2, ds2, prm, g, pop, fit, best, stream_id=5)
+    np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), straight[0].view(np.uint32))
+    np.testing.assert_array_equal(fit.cpu().numpy(), straight[1])
+    assert int(best.cpu()[0]) == straight[2]
+    c2.close()
+    ranks, nu = oracle.encode(X)
+    ref = oracle.de_run(ranks, nu, y, K, depth=depth, P=P, G=G, CR=0.7, seed=11, stream=5, dither=True,
+                        history=True)
+    np.testing.assert_array_equal(straight[0].view(np.uint32), ref["pop_hist"][G].view(np.uint32))
+    assert straight[2] == ref["best"]
+
+
 @pytest.mark.parametrize("case", DE_CASES, ids=[str(x[:4]) for x in DE_CASES])
 def test_de_trajectory_bit_exact(c, case):
     from paper_2311_06952_gb300 import deoct

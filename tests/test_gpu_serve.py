@@ -179,3 +179,28 @@ def test_engine_with_warm_starts_and_dither_equals_oracle():
         for k in ("kind", "a", "theta", "node_fit", "leaf_class"):
             np.testing.assert_array_equal(outs[i][k].astype(ref[k].dtype), ref[k], err_msg="set %d %s" % (i, k))
     assert st["completed"] == st["submissions"] > 0
+
+
+@pytest.mark.parametrize("engine", [True, False])
+def test_a_malformed_request_fails_alone(engine):
+    """A request whose features hold a NaN fails with the library's invalid-input error; the
+    requests around it, served by the same slots (and engine), still equal the oracle."""
+    from paper_2311_06952_gb300 import deoct
+    rs = _requests(num=4, seed=91, n_range=(2_000, 6_000), pop=16, gens=12)
+    bad = rs[1]
+    Xb = bad.X.copy()
+    Xb[len(Xb) // 2, 0] = np.nan
+    rs[1] = serve.FitRequest(X=Xb, y=bad.y, K=bad.K, depth=bad.depth, horizon=bad.horizon, pop=bad.pop,
+                             gens=bad.gens, seed=bad.seed, id=bad.id, arrival=bad.arrival)
+    srv = serve.Server(budget_bytes=32 << 30, slots=2, engine=engine)
+    try:
+        futs = [srv.submit(r) for r in rs]
+        with pytest.raises(deoct.DeoctError) as ei:
+            futs[1].result(timeout=300)
+        assert ei.value.code == deoct.DEOCT_ERR_INVALID
+        later = srv.submit(rs[0])  # the slot that saw the failure serves again
+        good = [futs[i].result(timeout=300) for i in (0, 2, 3)] + [later.result(timeout=300)]
+    finally:
+        srv.close()
+    for res, r in zip(good, [rs[0], rs[2], rs[3], rs[0]]):
+        _check(res, _oracle_tree(r))

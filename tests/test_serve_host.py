@@ -126,3 +126,29 @@ def test_admission_prefers_the_slot_that_already_holds_scratch():
     srv.close()
     assert len({r.slot for r in res}) == 1  # every request reused the first slot's scratch
     assert srv.peak_charged <= budget
+
+
+def test_a_failing_request_fails_alone():
+    """A fit that raises (the library's error for bad input, say) fails its own future; the
+    slot is freed, its charge returned, and the requests before and after it are served."""
+    log = []
+    good = _fake_fit(0.01, log)
+
+    def fit(slot, req):
+        if req.id == 3:
+            raise RuntimeError("injected failure of request 3")
+        return good(slot, req)
+
+    srv = serve.Server(budget_bytes=1 << 40, slots=2, fit_fn=fit)
+    futs = [srv.submit(_req(i)) for i in range(8)]
+    done = []
+    for i, f in enumerate(futs):
+        if i == 3:
+            with pytest.raises(RuntimeError, match="injected"):
+                f.result(timeout=30)
+        else:
+            done.append(f.result(timeout=30).id)
+    srv.close()
+    assert done == [0, 1, 2, 4, 5, 6, 7]
+    assert srv.running == 0 and srv.charged == sum(srv.retained)
+    assert sorted(srv.free_slots) == [0, 1]
