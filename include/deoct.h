@@ -348,6 +348,13 @@ DEOCT_API int deoct_get_memory(deoct_ctx* ctx, uint64_t* device_bytes, uint64_t*
 /* deoct_release_scratch: frees every scratch buffer of `ctx` (the next calls
  * allocate again).  Synchronises the device.  sync. */
 DEOCT_API int deoct_release_scratch(deoct_ctx* ctx);
+/* deoct_set_scratch_limit (no counterpart in the paper: a serving budget): caps
+ * the device bytes `ctx`'s scratch may hold, 0 = no cap (the default).  A call
+ * whose scratch would grow past the cap fails with DEOCT_ERR_OOM before it
+ * allocates or launches anything for that buffer; the context stays usable (raise
+ * the cap, or release scratch, and call again).  Buffers already held above a
+ * lowered cap are kept.  sync. */
+DEOCT_API int deoct_set_scratch_limit(deoct_ctx* ctx, uint64_t bytes);
 DEOCT_API int deoct_fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int32_t F, int32_t K,
                                       int32_t rank_bytes, const deoct_params* params,
                                       uint64_t* bytes_out);

@@ -31,12 +31,22 @@ int scratch_get(deoct_ctx* ctx, int slot, size_t bytes, void** out) {
   Scratch& s = ctx->scratch[slot];
   if (bytes == 0) bytes = 16;
   if (s.bytes < bytes) {
+    size_t want = bytes + bytes / 8;  // headroom against repeated growth
+    if (ctx->scratch_limit) {  // the buffer's growth must keep the total within the limit
+      size_t others = 0;
+      for (int i = 0; i < SL_COUNT; ++i)
+        if (i != slot) others += ctx->scratch[i].bytes;
+      if (others + bytes > ctx->scratch_limit)
+        return set_error(DEOCT_ERR_OOM,
+                         "scratch of %zu bytes would pass the context's limit of %zu bytes (%zu held "
+                         "in other buffers)", bytes, (size_t)ctx->scratch_limit, others);
+      want = std::min(want, (size_t)ctx->scratch_limit - others);
+    }
     if (s.ptr) {
       DEOCT_CUDA_TRY(cudaFree(s.ptr));  // synchronises the device: no pending use
       s.ptr = nullptr;
       s.bytes = 0;
     }
-    size_t want = bytes + bytes / 8;  // headroom against repeated growth
     cudaError_t e = cudaMalloc(&s.ptr, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -407,6 +417,14 @@ int deoct_get_memory(deoct_ctx* ctx, uint64_t* device_bytes, uint64_t* pinned_by
   for (int i = 0; i < SL_COUNT; ++i) d += ctx->scratch[i].bytes;
   if (device_bytes) *device_bytes = d;
   if (pinned_bytes) *pinned_bytes = ctx->h_pinned_bytes;
+  return DEOCT_OK;
+  API_END
+}
+
+int deoct_set_scratch_limit(deoct_ctx* ctx, uint64_t bytes) {
+  API_BEGIN
+  CTX_CHECK(ctx);
+  ctx->scratch_limit = bytes;
   return DEOCT_OK;
   API_END
 }

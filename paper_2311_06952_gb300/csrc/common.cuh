@@ -104,6 +104,7 @@ struct deoct_ctx {
   // evaluator launch shape forced by deoct_set_eval_config (0 = automatic)
   int force_S = 0, force_TG = 0, force_warps = 0, force_grid = 0;
   int force_stream = 0;  // deoct_set_eval_streaming: streaming kernel for every ballot launch
+  uint64_t scratch_limit = 0;  // deoct_set_scratch_limit: cap of the scratch held (0: none)
   // shared engine that runs the generations of this context's batched level
   // solves together with other contexts' (deoct_engine_attach; nullable)
   deoct_engine* engine = nullptr;

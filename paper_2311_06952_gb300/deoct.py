@@ -36,7 +36,7 @@ EXPORTED = [
     "deoct_eval_population_noalloc", "deoct_encode_ex", "deoct_split_values", "deoct_predict",
     "deoct_selftest_wait", "deoct_encode_auto", "deoct_engine_create", "deoct_engine_destroy",
     "deoct_engine_attach", "deoct_engine_get_stats", "deoct_get_memory", "deoct_fit_scratch_bound",
-    "deoct_release_scratch", "deoct_set_eval_streaming",
+    "deoct_release_scratch", "deoct_set_scratch_limit", "deoct_set_eval_streaming",
 ]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -105,6 +105,7 @@ def load(path: str | None = None):
             "deoct_get_memory": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
             "deoct_release_scratch": [_vp],
             "deoct_set_eval_streaming": [_vp, _i32],
+            "deoct_set_scratch_limit": [_vp, _u64],
             "deoct_fit_scratch_bound": [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(Params),
                                         ctypes.POINTER(_u64)],
             "deoct_engine_create": [ctypes.POINTER(_vp), _i32],
@@ -250,6 +251,10 @@ class Context:
     def release_scratch(self):
         """Free the context's device scratch (synchronises the device)."""
         _check(load().deoct_release_scratch(self.handle))
+
+    def set_scratch_limit(self, nbytes: int):
+        """Cap the device scratch the context may hold (0: no cap); growth past it is DEOCT_ERR_OOM."""
+        _check(load().deoct_set_scratch_limit(self.handle, int(nbytes)))
 
     def attach_engine(self, engine):
         """Run this context's batched level solves in `engine`'s shared launches (None detaches)."""

@@ -239,8 +239,14 @@ class Server:
                     out = self.fit_fn(slot, req)
                     held = int(out.get("scratch_bytes", before))
                 else:
-                    with torch.cuda.stream(stream):
-                        out = fit_on_stream(ctx, req, stream)
+                    # the library holds the slot to its charge: retained scratch plus the
+                    # reserve; growing past it would be DEOCT_ERR_OOM, not an overcommit
+                    ctx.set_scratch_limit(before + (cost - inp))
+                    try:
+                        with torch.cuda.stream(stream):
+                            out = fit_on_stream(ctx, req, stream)
+                    finally:
+                        ctx.set_scratch_limit(0)
                     held = ctx.memory()[0]
                 res = FitResult(req.id, out["a"], out["theta"], out["leaf_class"], out["kind"],
                                 out["node_fit"], t_submit=ts, t_admit=ta, t_done=self.now(), slot=slot,

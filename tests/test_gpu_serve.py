@@ -204,3 +204,31 @@ def test_a_malformed_request_fails_alone(engine):
         srv.close()
     for res, r in zip(good, [rs[0], rs[2], rs[3], rs[0]]):
         _check(res, _oracle_tree(r))
+
+
+def test_scratch_limit_fails_cleanly_and_the_context_recovers():
+    """A scratch cap below what a fit needs fails the fit with DEOCT_ERR_OOM before it
+    allocates; with the cap lifted the same context fits the oracle's tree, and with the cap
+    at the library's own bound the fit runs within it."""
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    r = _requests(num=1, seed=93, n_range=(20_000, 20_000), pop=16, gens=10)[0]
+    ctx = deoct.Context(0)
+    try:
+        ctx.set_scratch_limit(1 << 20)
+        with pytest.raises(deoct.DeoctError) as ei:
+            out = serve.fit_on_stream(ctx, r, torch.cuda.current_stream())
+        assert ei.value.code == deoct.DEOCT_ERR_OOM
+        ctx.set_scratch_limit(0)
+        out = serve.fit_on_stream(ctx, r, torch.cuda.current_stream())
+        ref = _oracle_tree(r)
+        for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
+            np.testing.assert_array_equal(np.asarray(out[k]).astype(ref[k].dtype), ref[k])
+        ctx.release_scratch()
+        bound = serve.scratch_bound(r, ctx=ctx) + ctx.memory()[0]
+        ctx.set_scratch_limit(bound)
+        out2 = serve.fit_on_stream(ctx, r, torch.cuda.current_stream())
+        assert ctx.memory()[0] <= bound
+        np.testing.assert_array_equal(np.asarray(out2["a"]), np.asarray(out["a"]))
+    finally:
+        ctx.close()
