@@ -233,6 +233,7 @@ static DEArgs de_args(const deoct_dataset* ds, const deoct_params* p, int64_t n_
   a.alpha = p->alpha;
   a.n_min = p->n_min;
   a.dither = (p->flags & DEOCT_DITHER_M) ? 1 : 0;
+  a.Kmax = ds->K;
   a.status = status;
   return a;
 }

@@ -72,19 +72,19 @@ __device__ void block_argmin(const double* __restrict__ fit, int P, int* best_s,
     red_i[warp] = bi;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {  // the warps' winners, reduced by one warp in the same order
     const int nw = (blockDim.x + 31) >> 5;
-    double f0 = red_f[0];
-    int i0 = red_i[0];
-    for (int w = 1; w < nw; ++w) {
-      int oi = red_i[w];
-      double of = red_f[w];
-      if (oi >= 0 && (i0 < 0 || fit_lt(of, f0, bits) || (!fit_lt(f0, of, bits) && oi < i0))) {
-        f0 = of;
-        i0 = oi;
+    bf = lane < nw ? red_f[lane] : 0.0;
+    bi = lane < nw ? red_i[lane] : -1;
+    for (int off = 16; off > 0; off >>= 1) {
+      double of = __shfl_down_sync(0xFFFFFFFFu, bf, off);
+      int oi = __shfl_down_sync(0xFFFFFFFFu, bi, off);
+      if (oi >= 0 && (bi < 0 || fit_lt(of, bf, bits) || (!fit_lt(bf, of, bits) && oi < bi))) {
+        bf = of;
+        bi = oi;
       }
     }
-    *best_s = i0;
+    if (lane == 0) *best_s = bi;
   }
   __syncthreads();
 }
@@ -133,16 +133,37 @@ __device__ double group_fitness(const uint32_t* __restrict__ c, const float* __r
                                 int sub, int G, uint32_t gm) {
   long long correct = 0;
   uint32_t v = 0, splits = 0;
-  for (int l = sub; l < L; l += G) {
-    uint32_t mx = 0;
-    int64_t nl = 0;
-    for (int k = 0; k < K; ++k) {
-      const uint32_t x = c[l * K + k];
-      mx = x > mx ? x : mx;
-      nl += x;
+  // the lane's counts (leaves sub, sub + G, ..., every class), sixteen loads in
+  // flight at a time: one after another they were a chain of memory round trips
+  const int nc = ((L - sub + G - 1) / G) * K;
+  int li = sub, ki = 0;  // leaf and class of the next count loaded
+  uint32_t mx = 0;
+  int64_t nl = 0;
+  int kr = 0;            // classes of the current leaf reduced so far
+  for (int e0 = 0; e0 < nc; e0 += 16) {
+    uint32_t x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      x[j] = e0 + j < nc ? c[li * K + ki] : 0u;
+      if (++ki == K) {
+        ki = 0;
+        li += G;
+      }
     }
-    correct += mx;
-    if (nl > 0 && nl < n_min) v += 1;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (e0 + j < nc) {
+        mx = x[j] > mx ? x[j] : mx;
+        nl += x[j];
+        if (++kr == K) {
+          correct += mx;
+          if (nl > 0 && nl < n_min) v += 1;
+          mx = 0;
+          nl = 0;
+          kr = 0;
+        }
+      }
+    }
   }
   for (int t = sub; t < B; t += G) splits += genes[t] >= 1.0f ? 1u : 0u;
   for (int o = G >> 1; o > 0; o >>= 1) {
@@ -258,6 +279,205 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   if (threadIdx.x == 0 && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
 }
 
+// The steady-state step (Eq. selection of generation g - 1's trials, then
+// generation g's trial vectors) when every individual has its own group of G
+// lanes (P G <= 512) and a lane holds at most four consecutive genes (2B <= 4G).
+// The general step waits on global memory once per gene or leaf in turn; here
+// the loads an individual needs that do not wait for the argmin (its class
+// counts, fitness, trial and population genes, and the genes of r1 and r2, whose
+// draws need no memory) are issued together, the argmin reads the fitness from
+// shared memory, and the decode reads the new genes and n_p there too.  The
+// values are those of the general step: integer sums in any order, the same
+// draws, one rounding per float operation, the same selection and argmin.
+constexpr int kFastP = 256, kFastM = 16, kFastC = 16;
+
+__global__ void __launch_bounds__(512) de_step_fast_kernel(const DEArgs a, int g_arg, int flags,
+                                                          int G) {
+  __shared__ double red_f[32];
+  __shared__ int red_i[32];
+  __shared__ int best_s;
+  __shared__ double fit_s[kFastP];
+  __shared__ unsigned char sel_s[kFastP];
+  __shared__ float u_s[kFastP * kFastM];
+  __shared__ uint32_t nu_s[kMaxF];
+  const DEProb& pb = prob_of(a);
+  const int P = a.P, B = (1 << a.depth) - 1, m = 2 * B, L = 1 << a.depth, K = pb.K;
+  const int sub = threadIdx.x & (G - 1);
+  const uint32_t gm = (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+  const int r = threadIdx.x / G;
+  const bool act = r < P;  // a whole group is active or not
+  const bool bits = a.alpha >= 0.0;
+  const int per = (m + G - 1) / G;
+  const int q0 = sub * per, q1 = min(m, q0 + per);
+  for (int f = threadIdx.x; f < pb.F; f += blockDim.x) nu_s[f] = pb.n_unique[f];
+
+  // ---- this individual's own data (one round of loads) ----------------------
+  // a lane's class counts: leaves sub, sub + G, ..., all K classes of each
+  const int nc = ((L - sub + G - 1) / G) * K;  // at most kFastC (checked at launch)
+  float tr[4], pr[4];
+  uint32_t cv[kFastC];
+  double fr = 0.0;
+  if (act) {
+    fr = pb.fit[r];
+    const float* trg = pb.trial + (int64_t)r * m;
+    const float* pog = pb.pop + (int64_t)r * m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j;
+      tr[j] = q < q1 ? trg[q] : 0.0f;
+      pr[j] = q < q1 ? pog[q] : 0.0f;
+    }
+    const uint32_t* c = pb.counts + (int64_t)r * L * K;
+    int li = sub, ki = 0;  // leaf and class of the next count loaded
+#pragma unroll
+    for (int e = 0; e < kFastC; ++e) {
+      cv[e] = e < nc ? c[li * K + ki] : 0u;
+      if (++ki == K) {
+        ki = 0;
+        li += G;
+      }
+    }
+  }
+
+  // ---- generation g's draws and the genes of r1 and r2 (no memory needed for
+  // the draws, so they run while the loads above are in flight) --------------
+  const int g = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
+  const bool trial = g >= 1 && g <= pb.G;
+  int r1 = 0, r2 = 0, qrand = 0;
+  float M = a.M, rq[4], t1[4], p1[4], t2[4], p2[4];
+  if (act && trial) {
+    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, pb.seed, pb.stream_id);
+    const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
+    const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
+    r1 = (int)below(x0, (uint32_t)(P - 1));
+    if (r1 >= r) r1 += 1;
+    r2 = (int)below(x1, (uint32_t)(P - 2));
+    const int lo = r < r1 ? r : r1, hi = r < r1 ? r1 : r;
+    if (r2 >= lo) r2 += 1;
+    if (r2 >= hi) r2 += 1;
+    qrand = (int)below(x2, (uint32_t)m);
+    if (a.dither) M = u01(x3);
+    const float* t1g = pb.trial + (int64_t)r1 * m;
+    const float* p1g = pb.pop + (int64_t)r1 * m;
+    const float* t2g = pb.trial + (int64_t)r2 * m;
+    const float* p2g = pb.pop + (int64_t)r2 * m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j;
+      const bool in = q < q1;
+      t1[j] = in ? t1g[q] : 0.0f;
+      p1[j] = in ? p1g[q] : 0.0f;
+      t2[j] = in ? t2g[q] : 0.0f;
+      p2[j] = in ? p2g[q] : 0.0f;
+    }
+    // gene q draws s = q + 4 from block s / 8: a lane's four genes touch at most two
+    U64x4 blk = blk0;
+    uint32_t cur = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t s = 4u + (uint32_t)(q0 + j);
+      if (q0 + j < q1 && (s >> 3) != cur) {
+        cur = s >> 3;
+        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, pb.seed, pb.stream_id);
+      }
+      rq[j] = u01(draw_from_block(blk, s));
+    }
+  }
+
+  // ---- the fitness of Section 3.2 from the counts (as group_fitness) ---------
+  double f = 0.0;
+  if (act) {
+    long long correct = 0;
+    uint32_t v = 0, splits = 0;
+    uint32_t mx = 0;
+    int64_t nl = 0;
+    int kr = 0;  // classes of the current leaf reduced so far
+#pragma unroll
+    for (int e = 0; e < kFastC; ++e) {
+      if (e < nc) {
+        mx = cv[e] > mx ? cv[e] : mx;
+        nl += cv[e];
+        if (++kr == K) {
+          correct += mx;
+          if (nl > 0 && nl < a.n_min) v += 1;
+          mx = 0;
+          nl = 0;
+          kr = 0;
+        }
+      }
+    }
+    if (a.alpha != 0.0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (q0 + j < q1 && q0 + j < B) splits += tr[j] >= 1.0f ? 1u : 0u;
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      correct += __shfl_xor_sync(gm, correct, o);
+      v += __shfl_xor_sync(gm, v, o);
+      splits += __shfl_xor_sync(gm, splits, o);
+    }
+    const int64_t errors = pb.n_valid - (int64_t)correct;
+    f = (a.alpha == 0.0) ? exact_double(errors + (int64_t)v)
+                         : __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(a.alpha, (double)splits));
+  }
+
+  // ---- Eq. selection, then the argmin over shared memory --------------------
+  bool take = false;
+  if (act) {
+    __syncwarp(gm);  // every lane has read fit[r] before it is rewritten
+    take = fit_le(f, fr, bits);  // ties go to the trial
+    if (sub == 0) pb.fit_trial[r] = f;
+    if (take) {
+      float* dst = pb.pop + (int64_t)r * m;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (q0 + j < q1) dst[q0 + j] = tr[j];
+      if (sub == 0) pb.fit[r] = f;
+    }
+    if (sub == 0) {
+      fit_s[r] = take ? f : fr;
+      sel_s[r] = take ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  block_argmin(fit_s, P, &best_s, red_f, red_i, bits);
+  if (threadIdx.x == 0) *pb.best = best_s;
+  if (!trial) return;  // device-driven replay past the last generation
+
+  // ---- generation g's trial vectors from the new population, decoded --------
+  if (act) {
+    const float ub_a = (float)(pb.F + 1);
+    const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
+    const float* sbg = pb.pop + (int64_t)best_s * m;  // the new population: copies are done
+    const bool sel1 = sel_s[r1] != 0, sel2 = sel_s[r2] != 0;
+    float* u = pb.trial + (int64_t)r * m;
+    float* us = u_s + r * m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j;
+      if (q < q1) {
+        const float s1 = sel1 ? t1[j] : p1[j], s2 = sel2 ? t2[j] : p2[j];
+        const float sr = take ? tr[j] : pr[j];
+        const float v = __fadd_rn(sbg[q], __fmul_rn(M, __fsub_rn(s1, s2)));
+        const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
+        const float uq = (rq[j] <= a.CR || q == qrand) ? vc : sr;
+        u[q] = uq;
+        us[q] = uq;
+      }
+    }
+    __syncwarp(gm);  // the group's genes are in shared memory before they are decoded
+    for (int t = sub; t < B; t += G) {
+      int av;
+      uint32_t th;
+      decode_gene_pair(us[t], us[B + t], pb.F, nu_s, &av, &th);
+      pb.nodes[(int64_t)r * B + t] = pack_node(av, th);
+    }
+  }
+  const int64_t total = (int64_t)P * L * K;  // every count was read before the barrier
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) pb.counts[e] = 0;
+  if (threadIdx.x == 0 && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
+}
+
 __global__ void decode_kernel(const float* __restrict__ genes, int P, int B, int F,
                               const uint32_t* __restrict__ n_unique, uint16_t* __restrict__ a_out,
                               uint32_t* __restrict__ th_out) {
@@ -320,6 +540,15 @@ int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream
   const int nprob = a.probs ? a.nprob : 1;
   if (nprob <= 0) return DEOCT_OK;
   const int lanes = lanes_for(a.P);
+  const int m = 2 * ((1 << a.depth) - 1);
+  const int L = 1 << a.depth;
+  if ((flags & DE_SELECT) && (flags & DE_TRIAL) && !(flags & DE_FIRST) && a.P * lanes <= 512 &&
+      a.P <= kFastP && m <= 4 * lanes && m <= kFastM && a.Kmax > 0 &&
+      ((L + lanes - 1) / lanes) * a.Kmax <= kFastC) {
+    de_step_fast_kernel<<<nprob, block_for(a.P * lanes), 0, s>>>(a, g, flags, lanes);
+    count_launch(ctx);
+    return check_launch("de_step_fast_kernel");
+  }
   de_step_kernel<<<nprob, block_for(a.P * lanes), 0, s>>>(a, g, flags, lanes);
   count_launch(ctx);
   return check_launch("de_step_kernel");

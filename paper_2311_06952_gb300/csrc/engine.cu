@@ -235,6 +235,7 @@ int rebuild(deoct_engine* e, const EngineGroupKey& k, Group& g) {
   a.alpha = k.alpha;
   a.n_min = k.n_min;
   a.dither = k.dither;
+  a.Kmax = Kmax;
   a.status = c->d_status;
   if (!c->cap_stream) DEOCT_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   const uint64_t l0 = c->launches, v0 = c->eval_launches;

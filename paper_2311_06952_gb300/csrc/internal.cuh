@@ -123,6 +123,7 @@ struct DEArgs {
   float M, CR;
   double alpha;
   int n_min, dither;
+  int Kmax;              // the largest K of the launch's problems (0: not known)
   int* status;
 };
 enum : int { DE_FIRST = 1, DE_SELECT = 2, DE_TRIAL = 4, DE_GEN_DEVICE = 8 };

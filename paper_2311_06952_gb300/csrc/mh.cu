@@ -585,6 +585,7 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
   a.alpha = prm->alpha;
   a.n_min = prm->n_min;
   a.dither = (prm->flags & DEOCT_DITHER_M) ? 1 : 0;
+  a.Kmax = K;
   a.status = ctx->d_status;
   DEOCT_TRY(de_launch_init(ctx, a, s));
 
