@@ -24,9 +24,15 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
       invariants of selection; the draw-to-index maps and the clamp are readings
       of the paper (its text fixes neither), pinned as stated;
   node_genes -- decodes back to every (a, theta) under Eq. aenc / Eq. benc;
+  greedy_tree -- the CART warm start: pinned to a float-threshold restatement
+      (brute force over midpoints, top down);
   mh -- pinned by special cases (horizon 1 = greedy misclassification tree,
       n_min >= n, single class) and by Algorithm 2 restated in Python over the
-      pinned de_run and depth1 (subsets induced on raw float thresholds).
+      pinned de_run and depth1 (subsets induced on raw float thresholds), with
+      and without the CART and DEOCT warm starts (restated over greedy_tree,
+      de_run and node_genes);
+  split_values, predict -- routing training samples on raw thresholds equals
+      routing ranks; the thresholds are the midpoints of the threshold set.
 """
 from __future__ import annotations
 

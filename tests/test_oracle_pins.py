@@ -809,3 +809,58 @@ def test_oracle_reproduces_golden_fixtures():
     for name, fn in (("deoct_workload0.json", mg.deoct_workload0), ("eval_workload1.json", mg.eval_workload1)):
         with open(os.path.join(here, name)) as f:
             assert fn() == json.load(f), name
+
+
+@pytest.mark.parametrize("cart,deo,seed", [(True, False, 3), (False, True, 4), (True, True, 5)])
+def test_mh_warm_starts_equal_algorithm2_composed_from_pinned_steps(cart, deo, seed):
+    """The warm starts of Algorithm 2 restated over the pinned steps: the DEOCT warm start is
+    the best tree of one full-depth DEOCT (Philox stream 0) on the whole set, and node t's
+    seed is its subtree at t with t's shape; the CART warm start is the greedy tree of depth
+    D_t on (X_t, Y_t); both encoded by node_genes (itself pinned to decode back), the DEOCT
+    seed first, then the CART seed, in the first slots of node t's DEOCT."""
+    w = datagen.make_workload(0, n=600)
+    X, y, K = w["X"][:, :5], w["y"], w["K"]
+    rng = _rng(seed)
+    y = np.where(rng.random(len(y)) < 0.1, 1 - y, y).astype(np.uint8)
+    ranks, nu = oracle.encode(X)
+    uniq = [np.unique(np.where(X[:, p] == 0, 0, X[:, p]).astype(np.float64)) for p in range(X.shape[1])]
+    depth, horizon, P, G = 4, 2, 8, 5
+    got = oracle.mh(ranks, nu, y, K, depth, horizon, P, G, seed=seed, cart_seeds=cart, de_seeds=deo)
+    B = (1 << depth) - 1
+    wa = wth = None
+    if deo:
+        full = oracle.de_run(ranks, nu, y, K, depth=depth, P=P, G=G, seed=seed, stream=0)
+        wa, wth = oracle.decode(full["pop"][full["best"]][None], depth, nu)
+        wa, wth = wa[0], wth[0]
+
+    def genes(a_, th_):
+        n_p = np.array([nu[x - 1] if x > 0 else 1 for x in a_], np.uint32)
+        ah, bh = oracle.node_genes(np.asarray(a_, np.int32), np.asarray(th_, np.uint32), n_p)
+        return np.concatenate([ah, bh]).astype(np.float32)
+
+    a = np.zeros(B, np.int64)
+    th = np.zeros(B, np.int64)
+    for t in range(1, B + 1):
+        d = t.bit_length() - 1
+        idx = np.nonzero(_np_route_to_depth(X, uniq, a, th, d) == t)[0].astype(np.int32)
+        if not (len(idx) > 1 and len(np.unique(y[idx])) > 1):
+            continue
+        Dt = min(horizon, depth - d)
+        if Dt >= 2:
+            seeds = []
+            if deo:  # the subtree at t: local level r, position j -> node (t << r) + j
+                nodes = [(t << r) + j for r in range(Dt) for j in range(1 << r)]
+                seeds.append(genes([wa[v - 1] for v in nodes], [wth[v - 1] for v in nodes]))
+            if cart:
+                ga, gt = oracle.greedy_tree(ranks, nu, y, K, Dt, idx=idx)
+                seeds.append(genes(ga, gt))
+            out = oracle.de_run(ranks, nu, y, K, depth=Dt, P=P, G=G, seed=seed, stream=t, idx=idx,
+                                seeds=np.stack(seeds))
+            dga, dgt = oracle.decode(out["pop"][out["best"]][None], Dt, nu)
+            a[t - 1], th[t - 1] = dga[0, 0], dgt[0, 0]
+        else:
+            a1, t1, _ = oracle.depth1(ranks, nu, y, K, idx=idx)
+            a[t - 1], th[t - 1] = a1, t1
+    np.testing.assert_array_equal(got["a"], a)
+    np.testing.assert_array_equal(got["theta"], th)
+    assert (got["kind"] == 2).sum() >= 3
