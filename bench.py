@@ -45,12 +45,12 @@ INT32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 lanes issue INT32
 # taken on: a hash of the re-laid evaluator kernel's code in csrc/eval.cu and of the
 # headers it is built from (eval_kernel.cuh, common.cuh), comments and whitespace
 # left out.
-EVAL_TRAFFIC = {"source_sha256_16": "1c9777c0fc1b083d", "bytes": 211_089_408 + 3_604_736,
+EVAL_TRAFFIC = {"source_sha256_16": "4c2a85aa0dc07e19", "bytes": 212_132_864 + 3_597_568,
                 # the same capture: issue rate (of 4 per SM per cycle), pipe and DRAM figures
-                "ncu": {"inst_per_cycle": 3.4621, "issue_frac": 0.8655, "alu_pipe_frac": 0.8132,
-                        "shared_pipe_frac": 2742438176 / 152 / (10.201984e-3 * 2.07e9),
-                        "inst_per_chunk": 34.23, "dram_gbs": (211_089_408 + 3_604_736) / 10.201984e-3 / 1e9,
-                        "dram_frac_of_peak": (211_089_408 + 3_604_736) / 10.201984e-3 / 1e9 / 6777.3}}
+                "ncu": {"inst_per_cycle": 3.4608, "issue_frac": 0.8652, "alu_pipe_frac": 0.8130,
+                        "shared_pipe_frac": 2742440261 / 152 / (10.224672e-3 * 2.07e9),
+                        "inst_per_chunk": 34.23, "dram_gbs": (212_132_864 + 3_597_568) / 10.224672e-3 / 1e9,
+                        "dram_frac_of_peak": (212_132_864 + 3_597_568) / 10.224672e-3 / 1e9 / 6777.3}}
 
 
 def _strip_comments(src):

@@ -85,11 +85,13 @@ __global__ void __launch_bounds__(1024, 1) eval_kernel(const __grid_constant__ E
 
     // ---- stage rank rows (and labels) ------------------------------------
     if (P.tma) {
-      if (!staged && warp == 0)
-        if (a.tmap_box)
-          issue_tile_boxes(a, P, s0, ns, W, stageb, lab_land, &mbar, lane);
-        else
-          issue_tile_tma(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane);
+      if (!staged) {  // (uniform across the CTA)
+        if (a.tmap_box) {
+          if (warp == 0) issue_tile_boxes(a, P, s0, ns, W, stageb, lab_land, &mbar, lane);
+        } else {
+          issue_tile_rows_cta(P, s0, ns, S, W, stageb, lab_land, a.lab_stage, &mbar, lane, warp, nw);
+        }
+      }
     } else {
       const RT* src = static_cast<const RT*>(P.ranks);
       for (int e = threadIdx.x; e < P.F * S; e += blockDim.x) {

@@ -534,6 +534,30 @@ __device__ __forceinline__ void issue_tile_tma(const EvalProb& P, int64_t s0, in
   }
 }
 
+// The same copies issued by the whole CTA (called by every thread): thread 0
+// arms the mbarrier, and after a CTA barrier lane l of warp w issues copy
+// w + nw l.  Issuing a copy costs its warp ~100 cycles, so the F row copies of
+// a wide uint32 tile no longer keep warp 0 (and with it the tile's end
+// barrier) behind the other warps.
+__device__ __forceinline__ void issue_tile_rows_cta(const EvalProb& P, int64_t s0, int ns, int S, int W,
+                                                    unsigned char* dst, unsigned char* labdst,
+                                                    int lab_stage, uint64_t* bar, int lane, int warp,
+                                                    int nw) {
+  const uint32_t bytes = ((uint32_t)ns * W + 15u) & ~15u;
+  const uint32_t lbytes = (uint32_t)tma_label_bytes(P, ns, lab_stage);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes * (uint32_t)P.F + lbytes);
+  __syncthreads();  // armed before any copy can complete
+  const unsigned char* src = static_cast<const unsigned char*>(P.ranks);
+  const int ncopy = P.F + (lbytes ? 1 : 0);
+  for (int c = warp + nw * lane; c < ncopy; c += 32 * nw) {
+    fence_proxy_async_smem();
+    if (c < P.F)
+      bulk_g2s(dst + (size_t)c * S * W, src + ((int64_t)c * P.ld + s0) * W, bytes, bar);
+    else
+      bulk_g2s(labdst, P.labels + s0, lbytes, bar);
+  }
+}
+
 // Stage a tile through the tensor map: boxes of tmap_box samples x F rows land
 // box-major -- box b at dst + b Fmax tmap_box W bytes, row f of a box at
 // f tmap_box W bytes (one box of the whole tile is the natural [F][S] order) --
