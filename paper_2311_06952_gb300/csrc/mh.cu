@@ -616,7 +616,12 @@ int de_batched(deoct_ctx* ctx, const deoct_dataset* ds, const Compacted& c,
       have = true;
     }
   const bool forced = ctx->force_S || ctx->force_TG || ctx->force_warps || ctx->force_grid || ctx->force_stream;
-  if (!have && !forced) {
+  // timing some twenty candidate shapes three times each costs a few milliseconds,
+  // which pays only on levels whose G + 1 evaluations are much longer than that:
+  // from 2e10 tree-sample evaluations (~20 ms on GB300) on; smaller levels take the
+  // chooser's shape
+  const bool worth = (double)nsum * P * (prm->gens + 1) >= 2e10;
+  if (!have && !forced && worth) {
     // candidates around the heuristic; each runs the real evaluation of S^1
     std::vector<EvalConfig> cands{cfg};  // the heuristic's own shape first
     for (int S : {256, 512, 1024, 2048})

@@ -212,3 +212,26 @@ def test_moving_horizon_streaming_kernel_forced_bit_exact(c):
         c.set_eval_streaming(False)
     for k in ("kind", "a", "theta", "node_fit", "leaf_class"):
         np.testing.assert_array_equal(out[k].astype(ref[k].dtype), ref[k], err_msg=k)
+
+
+def test_autotuned_level_solve_equals_plain_at_workload_size(c):
+    """The moving-horizon workload at its full size (n = 1e6, F = 30, D = 8, horizon 3,
+    P = 128, G = 200), where every level is large enough for the evaluator autotuner to time
+    its candidate shapes (32-warp CTAs, tiles between the powers of two): the batched fit
+    gives the plain per-node fit's tree (the plain form equals the oracle in the tests above,
+    at sizes the oracle finishes)."""
+    from paper_2311_06952_gb300 import deoct
+    w = datagen.make_workload(2)
+    ctx = deoct.Context(0)
+    try:
+        ds = gpu_dataset(ctx, w["X"], w["y"], w["K"], 4)
+        outs = []
+        for flags in (0, deoct.DEOCT_BATCHED):
+            prm = deoct.make_params(w["depth"], w["P"], w["G"], mut_f=w["M"], cr=w["CR"], seed=w["seed"],
+                                    horizon=w["horizon"], flags=flags)
+            outs.append(deoct.deoct_fit_moving_horizon(ctx, ds, prm))
+        for k in ("a", "theta", "kind", "node_fit", "leaf_class"):
+            np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
+        assert (outs[1]["kind"] == 2).sum() >= 60
+    finally:
+        ctx.close()
