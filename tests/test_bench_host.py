@@ -84,3 +84,25 @@ def test_source_key_covers_the_shape_chooser(tmp_path, monkeypatch):
     assert "25000.0 + 170.0 * copies" in text
     ev.write_text(text.replace("25000.0 + 170.0 * copies", "26000.0 + 170.0 * copies", 1))
     assert bench._eval_source_hash() != base
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    """`bench.py --impl reference` (the oracle on the host's cores, no GPU) prints one JSON
+    line on the main arm's metric, unit and direction, with its CPU baseline and an
+    end-to-end entry that copies nothing."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, cwd=root, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
