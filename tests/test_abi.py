@@ -45,6 +45,10 @@ def test_version_and_error_string_without_gpu(libpath):
     # a NULL context is rejected on the host, before any CUDA call
     assert lib.deoct_set_timing(None, 1) == deoct.DEOCT_ERR_INVALID
     assert b"context" in lib.deoct_last_error_string()
+    for call in (lambda: lib.deoct_set_scratch_limit(None, 1 << 20), lambda: lib.deoct_release_scratch(None),
+                 lambda: lib.deoct_set_eval_config(None, 0, 0, 0, 0),
+                 lambda: lib.deoct_set_eval_streaming(None, 1)):
+        assert call() == deoct.DEOCT_ERR_INVALID
 
 
 def test_struct_layouts_match_header():
