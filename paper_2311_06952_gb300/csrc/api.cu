@@ -189,6 +189,7 @@ struct DEBuffers {
   uint32_t* nodes;
   uint32_t* counts;
   int32_t* gen;
+  unsigned char* part;  // kDePartBytes: the split step's argmin candidates and generation
 };
 
 static int de_buffers(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_params* p, DEBuffers* b) {
@@ -198,6 +199,7 @@ static int de_buffers(deoct_ctx* ctx, const deoct_dataset* ds, const deoct_param
   DEOCT_TRY(scratch_get(ctx, SL_NODES, P * B * sizeof(uint32_t), (void**)&b->nodes));
   DEOCT_TRY(scratch_get(ctx, SL_COUNTS, P * L * ds->K * sizeof(uint32_t), (void**)&b->counts));
   DEOCT_TRY(scratch_get(ctx, SL_GEN, sizeof(int32_t), (void**)&b->gen));
+  DEOCT_TRY(scratch_get(ctx, SL_DE_PART, kDePartBytes, (void**)&b->part));
   return DEOCT_OK;
 }
 
@@ -235,6 +237,10 @@ static DEArgs de_args(const deoct_dataset* ds, const deoct_params* p, int64_t n_
   a.dither = (p->flags & DEOCT_DITHER_M) ? 1 : 0;
   a.Kmax = ds->K;
   a.status = status;
+  const int nblk = kMaxPop / kDeWideR;
+  a.part_f = reinterpret_cast<double*>(b.part);
+  a.part_i = reinterpret_cast<int*>(b.part + sizeof(double) * nblk);
+  a.part_g = reinterpret_cast<int*>(b.part + (sizeof(double) + sizeof(int)) * nblk);
   return a;
 }
 

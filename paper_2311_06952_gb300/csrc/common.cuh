@@ -73,6 +73,7 @@ enum ScratchSlot : int {
   SL_MH_D1KEYS, SL_MH_D1VALS, SL_MH_D1K1, SL_MH_D1V1, SL_MH_D1BEST, SL_MH_POP, SL_MH_FIT,
   SL_MH_BEST, SL_MH_HOSTBUF, SL_D1_RESULT, SL_MISC,
   SL_MH_RANKS2, SL_MH_LABELS2, SL_MH_IDX2, SL_MH_POS2, SL_MH_SUB, SL_MH_SUBHIST, SL_MH_SEEDS,
+  SL_DE_PART,
   SL_EVAL_ACC,  // zero at rest: ticket word, then the counts of one fused evaluation
   SL_COUNT
 };

@@ -178,6 +178,74 @@ __device__ double group_fitness(const uint32_t* __restrict__ c, const float* __r
   return __dadd_rn((double)(errors + (int64_t)v), __dmul_rn(alpha, (double)splits));
 }
 
+// Eq. selection of individual r by its group of G lanes: the fitness of its
+// just-evaluated trial from the class counts; the trial replaces the individual
+// when it is no worse (ties go to the trial).
+__device__ __forceinline__ void select_individual(const DEArgs& a, const DEProb& pb, int r, int B,
+                                                  int L, int K, int sub, int G, uint32_t gm,
+                                                  bool bits) {
+  const int m = 2 * B;
+  const float* genes = pb.trial + (int64_t)r * m;
+  const double f = group_fitness(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
+                                 a.n_min, a.alpha, sub, G, gm);
+  const double fr = pb.fit[r];
+  __syncwarp(gm);  // every lane has read fit[r] before it is rewritten
+  if (sub == 0) pb.fit_trial[r] = f;
+  if (fit_le(f, fr, bits)) {
+    float* dst = pb.pop + (int64_t)r * m;
+    for (int q = sub; q < m; q += G) dst[q] = genes[q];
+    if (sub == 0) pb.fit[r] = f;
+  }
+}
+
+// Generation g's trial vector of individual r (Eqs. mutation and crossover) from
+// the population and its best individual, stored with its decoded nodes.  Lane
+// `sub` of the group takes consecutive genes, which share Philox blocks.
+__device__ __forceinline__ void trial_individual(const DEArgs& a, const DEProb& pb, int r, int g,
+                                                 int best, int B, int sub, int G, uint32_t gm) {
+  const int P = a.P, m = 2 * B;
+  const float ub_a = (float)(pb.F + 1);
+  const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
+  const float* sb = pb.pop + (int64_t)best * m;
+  const int per = (m + G - 1) / G;
+  // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
+  const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, pb.seed, pb.stream_id);
+  const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
+  const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
+  int r1 = (int)below(x0, (uint32_t)(P - 1));
+  if (r1 >= r) r1 += 1;
+  int r2 = (int)below(x1, (uint32_t)(P - 2));
+  const int lo = r < r1 ? r : r1, hi = r < r1 ? r1 : r;
+  if (r2 >= lo) r2 += 1;
+  if (r2 >= hi) r2 += 1;
+  const int qrand = (int)below(x2, (uint32_t)m);
+  const float M = a.dither ? u01(x3) : a.M;
+  const float* s1 = pb.pop + (int64_t)r1 * m;
+  const float* s2 = pb.pop + (int64_t)r2 * m;
+  const float* sr = pb.pop + (int64_t)r * m;
+  float* u = pb.trial + (int64_t)r * m;
+  U64x4 blk = blk0;
+  uint32_t cur = 0;  // block held in blk
+  const int q0 = sub * per, q1 = min(m, q0 + per);
+  for (int q = q0; q < q1; ++q) {
+    const uint32_t s = 4u + (uint32_t)q;
+    if ((s >> 3) != cur) {
+      cur = s >> 3;
+      blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, pb.seed, pb.stream_id);
+    }
+    const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
+    const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
+    const float rq = u01(draw_from_block(blk, s));
+    u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
+  }
+  __syncwarp(gm);  // the group's genes are written before they are decoded
+  for (int t = sub; t < B; t += G) {
+    int av;
+    uint32_t th;
+    decode_gene_pair(u[t], u[B + t], pb.F, pb.n_unique, &av, &th);
+    pb.nodes[(int64_t)r * B + t] = pack_node(av, th);
+  }
+}
 
 // One CTA per subproblem; each individual is worked on by a group of `lanes`
 // consecutive threads (lanes x P <= blockDim.x, lanes <= 4), which shortens the
@@ -203,20 +271,12 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   if (flags & (DE_FIRST | DE_SELECT)) {
     const bool first = (flags & DE_FIRST) != 0;
     for (int r = r0; r < P; r += rstep) {
-      const float* genes = (first ? pb.pop : pb.trial) + (int64_t)r * m;
-      const double f = group_fitness(pb.counts + (int64_t)r * L * K, genes, B, L, K, pb.n_valid,
-                                     a.n_min, a.alpha, sub, G, gm);
       if (first) {
+        const double f = group_fitness(pb.counts + (int64_t)r * L * K, pb.pop + (int64_t)r * m, B,
+                                       L, K, pb.n_valid, a.n_min, a.alpha, sub, G, gm);
         if (sub == 0) pb.fit[r] = f;
       } else {
-        const double fr = pb.fit[r];
-        __syncwarp(gm);
-        if (sub == 0) pb.fit_trial[r] = f;
-        if (fit_le(f, fr, bits)) {  // Eq. selection: ties go to the trial
-          float* dst = pb.pop + (int64_t)r * m;
-          for (int q = sub; q < m; q += G) dst[q] = genes[q];
-          if (sub == 0) pb.fit[r] = f;
-        }
+        select_individual(a, pb, r, B, L, K, sub, G, gm, bits);
       }
     }
     __syncthreads();
@@ -231,49 +291,7 @@ __global__ void __launch_bounds__(1024) de_step_kernel(const DEArgs a, int g_arg
   const int g = g_s;
   if (g < 1 || g > pb.G) return;  // device-driven replay past the last generation
   const int best = best_s;
-  const float ub_a = (float)(pb.F + 1);
-  const float hi_a = below_bound(ub_a), hi_b = below_bound(1.0f);
-  const float* sb = pb.pop + (int64_t)best * m;
-  const int per = (m + G - 1) / G;  // consecutive genes per lane: they share Philox blocks
-  for (int r = r0; r < P; r += rstep) {
-    // draws 0..7 come from block 0: r1, r2, q_rand, M, genes 0..3
-    const U64x4 blk0 = philox4x64_10((uint64_t)g, (uint64_t)r, 0ull, 0ull, pb.seed, pb.stream_id);
-    const uint32_t x0 = draw_from_block(blk0, 0), x1 = draw_from_block(blk0, 1);
-    const uint32_t x2 = draw_from_block(blk0, 2), x3 = draw_from_block(blk0, 3);
-    int r1 = (int)below(x0, (uint32_t)(P - 1));
-    if (r1 >= r) r1 += 1;
-    int r2 = (int)below(x1, (uint32_t)(P - 2));
-    const int lo = r < r1 ? r : r1, hi = r < r1 ? r1 : r;
-    if (r2 >= lo) r2 += 1;
-    if (r2 >= hi) r2 += 1;
-    const int qrand = (int)below(x2, (uint32_t)m);
-    const float M = a.dither ? u01(x3) : a.M;
-    const float* s1 = pb.pop + (int64_t)r1 * m;
-    const float* s2 = pb.pop + (int64_t)r2 * m;
-    const float* sr = pb.pop + (int64_t)r * m;
-    float* u = pb.trial + (int64_t)r * m;
-    U64x4 blk = blk0;
-    uint32_t cur = 0;  // block held in blk
-    const int q0 = sub * per, q1 = min(m, q0 + per);
-    for (int q = q0; q < q1; ++q) {
-      const uint32_t s = 4u + (uint32_t)q;
-      if ((s >> 3) != cur) {
-        cur = s >> 3;
-        blk = philox4x64_10((uint64_t)g, (uint64_t)r, (uint64_t)cur, 0ull, pb.seed, pb.stream_id);
-      }
-      const float v = __fadd_rn(sb[q], __fmul_rn(M, __fsub_rn(s1[q], s2[q])));
-      const float vc = clamp_gene(v, q < B ? hi_a : hi_b);
-      const float rq = u01(draw_from_block(blk, s));
-      u[q] = (rq <= a.CR || q == qrand) ? vc : sr[q];
-    }
-    __syncwarp(gm);  // the group's genes are written before they are decoded
-    for (int t = sub; t < B; t += G) {
-      int av;
-      uint32_t th;
-      decode_gene_pair(u[t], u[B + t], pb.F, pb.n_unique, &av, &th);
-      pb.nodes[(int64_t)r * B + t] = pack_node(av, th);
-    }
-  }
+  for (int r = r0; r < P; r += rstep) trial_individual(a, pb, r, g, best, B, sub, G, gm);
   const int64_t total = (int64_t)P * L * K;
   for (int64_t e = threadIdx.x; e < total; e += blockDim.x) pb.counts[e] = 0;
   if (threadIdx.x == 0 && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
@@ -478,6 +496,65 @@ __global__ void __launch_bounds__(512) de_step_fast_kernel(const DEArgs a, int g
   if (threadIdx.x == 0 && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
 }
 
+// The steady-state step of one problem with a large population, split over CTAs
+// of kDeWideR individuals (kDeWideG lanes each) in two launches: one CTA alone
+// walks every individual through a chain of dependent loads, and at P = 1024
+// that took 88 us a generation.  The first launch does Eq. selection and the
+// argmin of each CTA's individuals; the second reduces those candidates to the
+// best (lowest index among minimal fitness, as one CTA would find it, since the
+// CTAs cover ascending index ranges), then builds the trials.  The values are
+// those of the one-CTA step.
+__global__ void __launch_bounds__(kDeWideR * kDeWideG) de_select_wide_kernel(const DEArgs a,
+                                                                              int g_arg, int flags) {
+  __shared__ double red_f[32];
+  __shared__ int red_i[32];
+  __shared__ int best_s;
+  const DEProb& pb = a.single;
+  const int P = a.P, B = (1 << a.depth) - 1, L = 1 << a.depth, K = pb.K;
+  constexpr int G = kDeWideG;
+  const int sub = threadIdx.x & (G - 1);
+  const uint32_t gm = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  const int r0 = blockIdx.x * kDeWideR, nr = min(kDeWideR, P - r0);
+  const int r = r0 + (int)threadIdx.x / G;
+  const bool bits = a.alpha >= 0.0;
+  if (r < P) select_individual(a, pb, r, B, L, K, sub, G, gm, bits);  // whole groups only
+  __syncthreads();
+  block_argmin(pb.fit + r0, nr, &best_s, red_f, red_i, bits);
+  if (threadIdx.x == 0) {
+    a.part_f[blockIdx.x] = pb.fit[r0 + best_s];
+    a.part_i[blockIdx.x] = r0 + best_s;
+    // the generation is read here, before the second launch's first CTA advances it
+    if (blockIdx.x == 0) *a.part_g = (flags & DE_GEN_DEVICE) ? *pb.gen : g_arg;
+  }
+}
+
+__global__ void __launch_bounds__(kDeWideR * kDeWideG) de_trial_wide_kernel(const DEArgs a,
+                                                                             int flags, int nblk) {
+  __shared__ double red_f[32];
+  __shared__ int red_i[32];
+  __shared__ int best_s;
+  const DEProb& pb = a.single;
+  const int P = a.P, B = (1 << a.depth) - 1, L = 1 << a.depth, K = pb.K;
+  constexpr int G = kDeWideG;
+  const int sub = threadIdx.x & (G - 1);
+  const uint32_t gm = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  const int r0 = blockIdx.x * kDeWideR, nr = min(kDeWideR, P - r0);
+  const int r = r0 + (int)threadIdx.x / G;
+  block_argmin(a.part_f, nblk, &best_s, red_f, red_i, a.alpha >= 0.0);
+  const int best = a.part_i[best_s];
+  const int g = *a.part_g;
+  const bool trial = g >= 1 && g <= pb.G;  // false: device-driven replay past the last generation
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *pb.best = best;
+    if (trial && (flags & DE_GEN_DEVICE)) *pb.gen = g + 1;
+  }
+  if (!trial) return;
+  if (r < P) trial_individual(a, pb, r, g, best, B, sub, G, gm);
+  // this CTA's individuals' class counts, read by the first launch, zeroed for the next
+  const int64_t e0 = (int64_t)r0 * L * K, e1 = (int64_t)(r0 + nr) * L * K;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) pb.counts[e] = 0;
+}
+
 __global__ void decode_kernel(const float* __restrict__ genes, int P, int B, int F,
                               const uint32_t* __restrict__ n_unique, uint16_t* __restrict__ a_out,
                               uint32_t* __restrict__ th_out) {
@@ -548,6 +625,16 @@ int de_launch_step(deoct_ctx* ctx, const DEArgs& a, int g, int flags, cudaStream
     de_step_fast_kernel<<<nprob, block_for(a.P * lanes), 0, s>>>(a, g, flags, lanes);
     count_launch(ctx);
     return check_launch("de_step_fast_kernel");
+  }
+  if ((flags & DE_SELECT) && (flags & DE_TRIAL) && !(flags & DE_FIRST) && !a.probs && a.part_f &&
+      a.P > kFastP && a.P <= kMaxPop) {
+    const int nblk = (a.P + kDeWideR - 1) / kDeWideR;
+    de_select_wide_kernel<<<nblk, kDeWideR * kDeWideG, 0, s>>>(a, g, flags);
+    count_launch(ctx);
+    DEOCT_TRY(check_launch("de_select_wide_kernel"));
+    de_trial_wide_kernel<<<nblk, kDeWideR * kDeWideG, 0, s>>>(a, flags, nblk);
+    count_launch(ctx);
+    return check_launch("de_trial_wide_kernel");
   }
   de_step_kernel<<<nprob, block_for(a.P * lanes), 0, s>>>(a, g, flags, lanes);
   count_launch(ctx);

@@ -125,8 +125,18 @@ struct DEArgs {
   int n_min, dither;
   int Kmax;              // the largest K of the launch's problems (0: not known)
   int* status;
+  // nullable: kDePartBytes of scratch for the split steady-state step of one problem
+  // with a large population (per-CTA argmin candidates, then the generation number)
+  double* part_f = nullptr;
+  int* part_i = nullptr;
+  int* part_g = nullptr;
 };
 enum : int { DE_FIRST = 1, DE_SELECT = 2, DE_TRIAL = 4, DE_GEN_DEVICE = 8 };
+// The split step: individuals per CTA and lanes per individual, and its scratch
+// (kMaxPop / kDeWideR candidates of 8 + 4 bytes, then the generation number).
+constexpr int kDeWideR = 32, kDeWideG = 8;
+constexpr size_t kDePartBytes = 2048;
+static_assert(kMaxPop / kDeWideR * 12 + 4 <= (int)kDePartBytes, "split-step scratch");
 
 int de_launch_init(deoct_ctx* ctx, const DEArgs& a, cudaStream_t s);
 // flags: DE_FIRST (fitness of the evaluated initial population), DE_SELECT

@@ -1245,6 +1245,7 @@ size_t fit_scratch_bound(const deoct_ctx* ctx, int64_t n, int F, int K, int W, c
   need(SL_NODES, 4.0 * P * Bf);
   need(SL_COUNTS, 4.0 * P * Lf * K);
   need(SL_GEN, 4);
+  need(SL_DE_PART, kDePartBytes);
   need(SL_MH_SEEDS, 4.0 * 2 * nn * 2 * B);
   need(SL_MH_SUB, 4.0 * npad);
   need(SL_MH_SUBHIST, 4.0 * pairs * K);

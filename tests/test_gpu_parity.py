@@ -432,6 +432,47 @@ def test_fit_subtree_with_seeds(c):
     assert f == ref["fit"][ref["best"]]
 
 
+# Populations above 256 take the split steady-state step (selection and per-CTA argmin, then
+# the best and the trials, over CTAs of 32 individuals).  Fits of fewer than three generations
+# issue its launches directly; longer ones replay them from the captured graph.
+# (case, depth, P, G, alpha, n_min, CR, dither, subset, n_seeds, seed, stream)
+WIDE_CASES = [
+    ("ragged_direct", 3, 300, 2, 0.0, 1, 0.9, False, False, 0, 5, 0),   # last CTA: 12 individuals
+    ("ragged_graph", 3, 300, 6, 0.5, 20, 0.7, True, True, 7, 6, 3),
+    ("one_in_last", 2, 257, 5, 0.0, 1, 0.9, False, False, 0, 7, 1),    # last CTA: 1 individual
+    ("neg_alpha", 4, 640, 4, -0.25, 1, 0.9, False, True, 0, 8, 2),     # doubles compared as values
+    ("max_pop", 4, 4096, 3, 0.0, 1, 0.9, True, False, 0, 9, 0),        # 128 CTAs of candidates
+]
+
+
+@pytest.mark.parametrize("case", WIDE_CASES, ids=[x[0] for x in WIDE_CASES])
+def test_fit_subtree_large_population_split_step_bit_exact(c, case):
+    import torch
+    from paper_2311_06952_gb300 import deoct
+    name, depth, P, G, alpha, n_min, CR, dither, subset, n_seeds, seed, stream = case
+    rng = _rng(300 + seed)
+    n, F, K = 2500, 6, 3
+    X = np.round(rng.random((n, F)), 2).astype(np.float32)
+    y = datagen.flip_labels(datagen.planted_tree_labels(X, 3, K, rng), K, 0.1, rng)
+    ds = gpu_dataset(c, X, y, K, 2)
+    ranks, nu = oracle.encode(X)
+    idx = np.sort(rng.choice(n, n // 2, replace=False)).astype(np.int32) if subset else None
+    seeds = datagen.random_genes(n_seeds, depth, F, rng) if n_seeds else None
+    ref = oracle.de_run(ranks, nu, y, K, depth=depth, P=P, G=G, CR=CR, alpha=alpha, n_min=n_min,
+                        seed=seed, stream=stream, dither=dither, idx=idx, seeds=seeds)
+    prm = deoct.make_params(depth, P, G, cr=CR, alpha=alpha, n_min=n_min, seed=seed,
+                            flags=deoct.DEOCT_DITHER_M if dither else 0)
+    pop = torch.empty((P, 2 * ((1 << depth) - 1)), dtype=torch.float32, device="cuda")
+    a, th, f = deoct.deoct_fit_subtree(c, ds, prm, stream_id=stream, pop_out=pop,
+                                       sample_idx=None if idx is None else to_dev(idx),
+                                       seeds=None if seeds is None else to_dev(seeds))
+    np.testing.assert_array_equal(pop.cpu().numpy().view(np.uint32), ref["pop"].view(np.uint32))
+    assert f == ref["fit"][ref["best"]]
+    a_ref, th_ref = oracle.decode(ref["pop"][ref["best"]][None], depth, nu)
+    np.testing.assert_array_equal(a.astype(np.int32), a_ref[0])
+    np.testing.assert_array_equal(th, th_ref[0])
+
+
 def test_de_workload3_reduced_bit_exact(c):
     """Large-scale DE shape (F=10, K=2, depth 4, P=1024, uint16 ranks) on 60k samples, 3 generations."""
     from paper_2311_06952_gb300 import deoct
