@@ -6,7 +6,9 @@
 //   DE_SELECT fitness of the just-evaluated trials, Eq. selection, best;
 //   DE_TRIAL  trial vectors of generation g from (population, best), their
 //             decoded nodes for the evaluator, and zeroed class counts.
-// So one generation is two launches: evaluator, step(SELECT|TRIAL).  Gene
+// So one generation is two launches: evaluator, step(SELECT|TRIAL); for one
+// problem with more than 256 individuals the step(SELECT|TRIAL) is itself split
+// over CTAs in two launches (de_select_wide_kernel, de_trial_wide_kernel).  Gene
 // arithmetic is float32 with one rounding per operation (__fsub_rn, __fmul_rn,
 // __fadd_rn); random numbers come from Philox4x64-10 keyed by (seed, stream).
 #include "internal.cuh"
